@@ -1,0 +1,233 @@
+/*
+ * nq.h -- C ABI of libnq: exact N-Queens solution counting on GB300 (sm_103a)
+ * by bitmask iterative depth-first search over independent prefix subtrees.
+ *
+ * Method: Yao & Li, "High-Performance N-Queens Solver on GPU: Iterative DFS
+ * with Zero Bank Conflicts" (arXiv 2511.12009).
+ *   - Somers bitmask state (cur/left/right, lowest-set-bit selection):
+ *     Section 2, Algorithm 1.
+ *   - Decomposition into subproblems by pre-placing the first d rows, with
+ *     first-row half symmetry and the odd-N centre rule: Section 1, Section 2.
+ *   - Iterative DFS with an explicit per-thread stack: Section 2, Algorithm 2.
+ *   - Last-row optimisation (count popc(valid) at row N-2 instead of pushing):
+ *     Section 3.2.3 (Approach 3), Algorithm 3.
+ *   - 64-bit result; 28 is the last N whose count fits: Section 4.5.
+ *
+ * Conventions shared by every entry point:
+ *   - Return value: NQ_OK (0) or a negative NQ_E* code; nq_strerror() names it.
+ *     Nothing exits, traps or throws across this boundary.
+ *   - Pointers named d_* are device pointers (cudaMalloc'd or torch tensors'
+ *     data_ptr) owned by the caller; pointers named h_* or out are host memory
+ *     owned by the caller. The library keeps no reference after a call returns
+ *     (asynchronous calls: until the stream reaches the call's work).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream). Asynchronous entry points enqueue work on it and return; errors
+ *     the kernels find are recorded in a per-device status word that
+ *     nq_sync() returns and clears.
+ *   - N is in 1..NQ_MAX_N (bit b of a mask is column b, so N <= 31).
+ *   - Thread safety: calls on different streams may run concurrently.
+ */
+#ifndef NQ_H
+#define NQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NQ_MAX_N 31
+
+/* status codes */
+#define NQ_OK 0
+#define NQ_EINVAL (-1)    /* bad argument, malformed prefix record, N mismatch */
+#define NQ_ENOMEM (-2)    /* host or device allocation failed */
+#define NQ_ECUDA (-3)     /* a CUDA runtime call failed (no device, launch error...) */
+#define NQ_EOVERFLOW (-4) /* the result does not fit 64 bits (N >= 29), or a cap was too small */
+#define NQ_ETIMEOUT (-5)  /* a bounded device wait ran out */
+#define NQ_ESTACK (-6)    /* a prefix needs more stack levels than the launch provides */
+#define NQ_EBUSY (-7)     /* the object is in use (e.g. a server slot table is full) */
+
+/*
+ * One subproblem: the Somers state after queens were placed in rows 0..d-1
+ * (Section 2: the (cur, left, right) triplets produced by pre-placing rows).
+ *   cols  bit c set when some placed queen is in column c        ("cur")
+ *   ld    columns of row d attacked along a left diagonal, & (2^N - 1)
+ *   rd    columns of row d attacked along a right diagonal        ("right")
+ *   meta  bits 0-1 weight (1 or 2: the symmetry multiplicity, Section 1)
+ *         bits 2-6 N, bits 7-11 d (= popcount(cols)), bits 12-31 tag
+ *         (0 for plain use; a request slot in the server).
+ * 16 bytes, 16-byte aligned in arrays.
+ */
+typedef struct nq_prefix {
+    uint32_t cols, ld, rd, meta;
+} nq_prefix;
+
+#define NQ_META(weight, n, d, tag)                                              \
+    ((uint32_t)(weight) | ((uint32_t)(n) << 2) | ((uint32_t)(d) << 7) |         \
+     ((uint32_t)(tag) << 12))
+#define NQ_META_WEIGHT(m) ((uint32_t)(m) & 3u)
+#define NQ_META_N(m) (((uint32_t)(m) >> 2) & 31u)
+#define NQ_META_D(m) (((uint32_t)(m) >> 7) & 31u)
+#define NQ_META_TAG(m) ((uint32_t)(m) >> 12)
+
+/* A queen on the board: row and column, both 0-based. */
+typedef struct nq_queen {
+    int8_t row, col;
+} nq_queen;
+
+/* Shared-memory stack layouts of the search kernel (the autotuner's axis).
+ * All of them interleave the per-thread stacks by thread, so that the 32 (or
+ * 8 per 128-byte phase) lanes of a warp always touch distinct banks, whatever
+ * depth each lane is at (Section 3.1's conflict-free idea). */
+#define NQ_LAYOUT_DEFAULT 0
+#define NQ_LAYOUT_PAPER 1 /* Algorithm 2 + Algorithm 3: 16-byte frames, the top frame
+                             re-read from shared memory every step */
+#define NQ_LAYOUT_REG 2   /* 16-byte frames, the top frame kept in registers; a frame
+                             is saved only while it still has untried columns */
+
+/* Launch configuration. Zero in any field selects the library default. */
+typedef struct nq_config {
+    int32_t layout;        /* NQ_LAYOUT_* */
+    int32_t block;         /* threads per block, a multiple of 32, <= 1024 */
+    int32_t blocks_per_sm; /* resident blocks per SM (grid = SMs x this); capped at
+                              what fits */
+    int32_t order;         /* 0: prefixes claimed in index order; 1: last index first */
+    int32_t d;             /* nq_total_ex only: prefix depth 1..N (0 = default) */
+    int32_t reserved[3];
+} nq_config;
+
+/* Timing of one nq_total_ex call, host wall clock in milliseconds. */
+typedef struct nq_timing {
+    double enumerate_ms; /* host prefix enumeration */
+    double upload_ms;    /* host -> device copy of the prefixes */
+    double kernel_ms;    /* the search kernel, CUDA events on the call's stream */
+    double total_ms;     /* whole call */
+    uint64_t prefixes;   /* number of subproblems */
+    int32_t d;           /* depth used */
+    int32_t layout;      /* layout used */
+    int32_t block;       /* block size used */
+    int32_t grid;        /* blocks launched */
+} nq_timing;
+
+/* ------------------------------------------------------------------------- */
+/* Host-side prefix generation (Section 1; Section 2, Algorithm 1 cut at     */
+/* depth d).                                                                 */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * Enumerate the symmetric depth-d prefix set of an N x N board into `out`
+ * (host, caller-owned, `cap` records), in canonical order: depth-first, rows
+ * top-down, columns (bits) increasing at every row. Row 0 takes columns
+ * 0..floor(N/2)-1 with weight 2; for odd N row 0 also takes the centre column
+ * m with the row-1 queen in columns 0..m-2, weight 2 (weight 1 when d = 1).
+ * d = 0 gives the single empty prefix with weight 1.
+ * out == NULL: size query, only *n_out is written. If cap is smaller than the
+ * set, the first cap records are written, *n_out gets the set's size and
+ * NQ_EOVERFLOW is returned. 0 <= d <= N.
+ */
+int nq_enumerate_prefixes(int N, int d, nq_prefix *out, uint64_t cap, uint64_t *n_out);
+
+/*
+ * The prefixes at canonical indices ranks[0..k-1] of the depth-d set (host
+ * arrays, caller-owned). A rank outside the set gives NQ_EINVAL (and a zero
+ * record in that slot).
+ */
+int nq_prefixes_at_ranks(int N, int d, const uint64_t *ranks, uint64_t k, nq_prefix *out);
+
+/*
+ * All descendants `rows` rows below one prefix (host), in canonical order, with
+ * the parent's weight: the prefixes of depth d+rows whose first d rows are the
+ * parent's. Same cap / size-query contract as nq_enumerate_prefixes.
+ */
+int nq_descendants(const nq_prefix *parent, int rows, nq_prefix *out, uint64_t cap,
+                   uint64_t *n_out);
+
+/* Default prefix depth the library uses for a board of size N. */
+int nq_default_depth(int N);
+
+/* ------------------------------------------------------------------------- */
+/* Device search (Algorithm 2 with Algorithm 3's last-row rule).             */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * Count the solutions below each of n prefixes of one board size N, every
+ * prefix with at least d rows placed. d_counts[i] = solutions below
+ * d_prefixes[i] (raw, no weight). Asynchronous on `stream`; allocates its
+ * small per-call work cursor stream-ordered and frees it the same way.
+ * Records that are malformed (N mismatch, bad weight, depth below d) get count
+ * 0 and set NQ_EINVAL / NQ_ESTACK in the status that nq_sync() returns.
+ */
+int nq_count(int N, int d, const nq_prefix *d_prefixes, uint64_t n, uint64_t *d_counts,
+             void *stream);
+
+/*
+ * General form: prefixes may mix board sizes (each record's meta holds N).
+ *   d_counts  optional [n]: solutions below each prefix
+ *   d_nodes   optional [n]: search nodes below each prefix (a node is one queen
+ *             placement in rows d..N-1); requesting it runs the diagnostic
+ *             build of the kernel, which also checks every stack access
+ *   d_totals  optional [32]: d_totals[N] += weight x solutions, for each prefix
+ *             of board size N (the caller zeroes it)
+ *   min_d     smallest depth among the prefixes (sizes the stack)
+ *   max_n     largest N among the prefixes (sizes the stack)
+ *   cfg       optional launch configuration (NULL = defaults)
+ */
+int nq_count_ex(const nq_prefix *d_prefixes, uint64_t n, int min_d, int max_n,
+                uint64_t *d_counts, uint64_t *d_nodes, uint64_t *d_totals,
+                const nq_config *cfg, void *stream);
+
+/*
+ * Wait for `stream` and return the first error any kernel of this library
+ * recorded on the current device since the last nq_sync (then clear it), or a
+ * CUDA error of the stream, or NQ_OK.
+ */
+int nq_sync(void *stream);
+
+/*
+ * Q(N), the number of solutions of the N-Queens problem, synchronously:
+ * enumerate (default depth), upload, search, sum weight x count. 1 <= N <= 28;
+ * N >= 29 returns NQ_EOVERFLOW (the count exceeds 64 bits, Section 4.5).
+ */
+int nq_total(int N, uint64_t *total_out);
+
+/*
+ * nq_total with a chosen configuration (cfg == NULL or cfg->d == 0: the
+ * default depth). nodes_out (optional) runs the diagnostic kernel build and
+ * returns the search nodes below all prefixes (unweighted). timing optional.
+ */
+int nq_total_ex(int N, const nq_config *cfg, uint64_t *total_out, uint64_t *nodes_out,
+                nq_timing *timing);
+
+/*
+ * Solutions of the N x N board that contain every listed queen (partial-board
+ * constraints; not in the paper, the serving extension). q[i] outside the
+ * board is NQ_EINVAL; the same cell twice counts once; two listed queens that
+ * attack each other (or share a row) give 0. Synchronous.
+ */
+int nq_count_constrained(int N, const nq_queen *q, int k, uint64_t *count_out);
+
+/* ------------------------------------------------------------------------- */
+/* Measurement (not in the paper): the integer roofline's denominator.        */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * Issue-rate microbenchmark of one 32-bit integer instruction on the current
+ * device: a full-occupancy grid where each thread runs 8 independent chains of
+ * it for 128 x iters steps. kind: 0 three-input logic (lop3), 1 add,
+ * 2 funnel shift, 3 popc, 4 the four-instruction lowest-bit pick
+ * (neg, and, xor, or). Writes PTX instructions per clock per SM, per second
+ * (whole GPU) and the SM clock in MHz seen over the run. Synchronous;
+ * allocates and frees its own small buffers.
+ */
+int nq_probe_alu(int kind, int iters, double *per_clk_per_sm, double *per_s, double *sm_mhz);
+
+/* Name of a status code (static string). */
+const char *nq_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* NQ_H */

@@ -1,0 +1,321 @@
+// api.cu -- the extern "C" entry points of libnq (declared in include/nq.h).
+#include <chrono>
+#include <cstring>
+#include <memory>
+#include <vector>
+
+#include "nq_internal.h"
+
+using namespace nqi;
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double ms_since(Clock::time_point t0) {
+    return std::chrono::duration<double, std::milli>(Clock::now() - t0).count();
+}
+
+bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
+
+int cuda_rc(cudaError_t e) { return e == cudaSuccess ? NQ_OK : NQ_ECUDA; }
+
+// Pinned host staging buffer, one per host thread (grown on demand).
+struct PinnedBuf {
+    void *p = nullptr;
+    size_t cap = 0;
+    ~PinnedBuf() {
+        if (p) cudaFreeHost(p);
+    }
+    void *get(size_t bytes) {
+        if (bytes <= cap) return p;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        cap = 0;
+        if (cudaMallocHost(&p, bytes) != cudaSuccess) {
+            p = nullptr;
+            return nullptr;
+        }
+        cap = bytes;
+        return p;
+    }
+};
+thread_local PinnedBuf t_stage;
+
+// Owns a non-blocking stream and the stream-ordered device allocations of one
+// synchronous call.
+struct CallCtx {
+    cudaStream_t s = nullptr;
+    std::vector<void *> bufs;
+    ~CallCtx() {
+        if (s) {
+            for (void *b : bufs) cudaFreeAsync(b, s);
+            cudaStreamSynchronize(s);
+            cudaStreamDestroy(s);
+        }
+    }
+    int init() { return cuda_rc(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking)); }
+    template <typename T>
+    int alloc(T **out, size_t bytes) {
+        void *p = nullptr;
+        if (cudaMallocAsync(&p, bytes ? bytes : 16, s) != cudaSuccess) return NQ_ENOMEM;
+        bufs.push_back(p);
+        *out = static_cast<T *>(p);
+        return NQ_OK;
+    }
+};
+
+// Enqueue one search over device-resident prefixes (shared by nq_count*,
+// nq_total_ex and nq_count_constrained).
+int enqueue_search(const nq_prefix *d_prefixes, uint64_t n, int expect_n, int min_d, int max_n,
+                   uint64_t *d_counts, uint64_t *d_nodes, uint64_t *d_totals,
+                   const nq_config *cfg, const uint32_t *allowed, cudaStream_t s, Plan *used) {
+    if (n == 0) return NQ_OK;
+    if (!d_prefixes || !aligned(d_prefixes, 16) || (d_counts && !aligned(d_counts, 8)) ||
+        (d_nodes && !aligned(d_nodes, 8)) || (d_totals && !aligned(d_totals, 8)))
+        return NQ_EINVAL;
+    const bool diag = d_nodes != nullptr;
+    const bool constrained = allowed != nullptr;
+    Plan p;
+    int rc = make_plan(max_n, min_d, diag, constrained, cfg, &p);
+    if (rc) return rc;
+    unsigned long long *cursor = nullptr;
+    if (cudaMallocAsync(reinterpret_cast<void **>(&cursor), sizeof(*cursor), s) != cudaSuccess)
+        return NQ_ENOMEM;
+    rc = cuda_rc(cudaMemsetAsync(cursor, 0, sizeof(*cursor), s));
+    if (!rc) {
+        SearchArgs a{};
+        a.pre = d_prefixes;
+        a.n = n;
+        a.counts = d_counts;
+        a.nodes = d_nodes;
+        a.totals = d_totals;
+        a.cursor = cursor;
+        a.expect_n = expect_n;
+        a.min_d = min_d;
+        a.slots = p.slots;
+        a.order = cfg ? cfg->order : 0;
+        if (allowed) std::memcpy(a.allowed, allowed, sizeof(a.allowed));
+        rc = launch_search(a, p, diag, constrained, s);
+    }
+    cudaFreeAsync(cursor, s);
+    if (used) *used = p;
+    return rc;
+}
+
+}  // namespace
+
+extern "C" const char *nq_strerror(int code) {
+    switch (code) {
+        case NQ_OK: return "ok";
+        case NQ_EINVAL: return "invalid argument or malformed prefix record";
+        case NQ_ENOMEM: return "out of memory";
+        case NQ_ECUDA: return "CUDA runtime error";
+        case NQ_EOVERFLOW: return "result or buffer overflow";
+        case NQ_ETIMEOUT: return "bounded device wait timed out";
+        case NQ_ESTACK: return "prefix needs more stack levels than the launch provides";
+        case NQ_EBUSY: return "busy";
+        default: return "unknown status code";
+    }
+}
+
+extern "C" int nq_count_ex(const nq_prefix *d_prefixes, uint64_t n, int min_d, int max_n,
+                           uint64_t *d_counts, uint64_t *d_nodes, uint64_t *d_totals,
+                           const nq_config *cfg, void *stream) {
+    if (max_n < 1 || max_n > NQ_MAX_N || min_d < 0 || min_d > max_n) return NQ_EINVAL;
+    return enqueue_search(d_prefixes, n, 0, min_d, max_n, d_counts, d_nodes, d_totals, cfg,
+                          nullptr, static_cast<cudaStream_t>(stream), nullptr);
+}
+
+extern "C" int nq_count(int N, int d, const nq_prefix *d_prefixes, uint64_t n,
+                        uint64_t *d_counts, void *stream) {
+    if (N < 1 || N > NQ_MAX_N || d < 0 || d > N || !d_counts) return NQ_EINVAL;
+    return enqueue_search(d_prefixes, n, N, d, N, d_counts, nullptr, nullptr, nullptr, nullptr,
+                          static_cast<cudaStream_t>(stream), nullptr);
+}
+
+extern "C" int nq_sync(void *stream) {
+    if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return NQ_ECUDA;
+    return take_device_status();
+}
+
+extern "C" int nq_total_ex(int N, const nq_config *cfg, uint64_t *total_out, uint64_t *nodes_out,
+                           nq_timing *timing) {
+    const auto t_start = Clock::now();
+    if (N < 1 || N > NQ_MAX_N || !total_out) return NQ_EINVAL;
+    if (N >= 29) return NQ_EOVERFLOW;  // Q(29) > 2^64 (Section 4.5: int64 ends at N = 28)
+    const int d = (cfg && cfg->d > 0) ? cfg->d : nq_default_depth(N);
+    if (d < 0 || d > N) return NQ_EINVAL;
+
+    // a1: host enumeration into pinned staging memory
+    const auto t_enum = Clock::now();
+    uint64_t np = 0;
+    int rc = nq_enumerate_prefixes(N, d, nullptr, 0, &np);
+    if (rc) return rc;
+    nq_prefix *h_pre = static_cast<nq_prefix *>(t_stage.get((np ? np : 1) * sizeof(nq_prefix)));
+    if (!h_pre) return NQ_ENOMEM;
+    uint64_t got = 0;
+    rc = nq_enumerate_prefixes(N, d, h_pre, np, &got);
+    if (rc) return rc;
+    const double enum_ms = ms_since(t_enum);
+
+    CallCtx ctx;
+    if ((rc = ctx.init())) return rc;
+    nq_prefix *d_pre = nullptr;
+    uint64_t *d_tot = nullptr, *d_nodes = nullptr;
+    if ((rc = ctx.alloc(&d_pre, np * sizeof(nq_prefix)))) return rc;
+    if ((rc = ctx.alloc(&d_tot, 32 * sizeof(uint64_t)))) return rc;
+    if (nodes_out && (rc = ctx.alloc(&d_nodes, np * sizeof(uint64_t)))) return rc;
+    cudaEvent_t ev[4];
+    for (auto &e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) return NQ_ECUDA;
+    struct EvGuard {
+        cudaEvent_t *e;
+        ~EvGuard() {
+            for (int i = 0; i < 4; ++i) cudaEventDestroy(e[i]);
+        }
+    } evg{ev};
+
+    // a2: upload; a3-a4: search and per-warp reduction; a5: the weighted total
+    cudaEventRecord(ev[0], ctx.s);
+    rc = cuda_rc(cudaMemcpyAsync(d_pre, h_pre, np * sizeof(nq_prefix), cudaMemcpyHostToDevice,
+                                 ctx.s));
+    if (!rc) rc = cuda_rc(cudaMemsetAsync(d_tot, 0, 32 * sizeof(uint64_t), ctx.s));
+    cudaEventRecord(ev[1], ctx.s);
+    Plan p{};
+    if (!rc)
+        rc = enqueue_search(d_pre, np, N, d, N, nullptr, d_nodes, d_tot, cfg, nullptr, ctx.s, &p);
+    cudaEventRecord(ev[2], ctx.s);
+    uint64_t tot = 0;
+    if (!rc)
+        rc = cuda_rc(cudaMemcpyAsync(&tot, d_tot + N, sizeof(uint64_t), cudaMemcpyDeviceToHost,
+                                     ctx.s));
+    cudaEventRecord(ev[3], ctx.s);
+    if (cudaStreamSynchronize(ctx.s) != cudaSuccess) return NQ_ECUDA;
+    if (rc) return rc;
+    const int st = take_device_status();
+    if (st) return st;
+    *total_out = tot;
+    if (nodes_out) {
+        std::vector<uint64_t> nodes(np);
+        if (np && cudaMemcpy(nodes.data(), d_nodes, np * sizeof(uint64_t),
+                             cudaMemcpyDeviceToHost) != cudaSuccess)
+            return NQ_ECUDA;
+        uint64_t s = 0;
+        for (uint64_t v : nodes) s += v;
+        *nodes_out = s;
+    }
+    if (timing) {
+        float up = 0, kern = 0;
+        cudaEventElapsedTime(&up, ev[0], ev[1]);
+        cudaEventElapsedTime(&kern, ev[1], ev[2]);
+        timing->enumerate_ms = enum_ms;
+        timing->upload_ms = up;
+        timing->kernel_ms = kern;
+        timing->prefixes = np;
+        timing->d = d;
+        timing->layout = p.layout;
+        timing->block = p.block;
+        timing->grid = p.grid;
+        timing->total_ms = ms_since(t_start);
+    }
+    return NQ_OK;
+}
+
+extern "C" int nq_total(int N, uint64_t *total_out) {
+    return nq_total_ex(N, nullptr, total_out, nullptr, nullptr);
+}
+
+// ---------------------------------------------------------------------------
+// Partial-board constraints: every listed queen's row may take only its
+// column, every other row loses the cells the listed queens attack. The
+// prefix rows are enumerated under the same masks (no symmetry: weight 1) and
+// the constrained kernel applies the masks below the prefix.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct CWalker {
+    int n, d;
+    uint32_t last;
+    const uint32_t *allowed;
+    std::vector<nq_prefix> *out;
+    void rec(int row, uint32_t cols, uint32_t ld, uint32_t rd) {
+        if (row == d) {
+            out->push_back(nq_prefix{cols, ld & last, rd, meta_of(1, n, d)});
+            return;
+        }
+        uint32_t av = last & ~(cols | ld | rd) & allowed[row];
+        while (av) {
+            const uint32_t p = av & (0u - av);
+            av ^= p;
+            rec(row + 1, cols | p, ((ld | p) << 1) & last, (rd | p) >> 1);
+        }
+    }
+};
+
+}  // namespace
+
+extern "C" int nq_count_constrained(int N, const nq_queen *q, int k, uint64_t *count_out) {
+    if (N < 1 || N > kMaxConstrainedN || k < 0 || k > 32 || (k && !q) || !count_out)
+        return NQ_EINVAL;
+    const uint32_t last = (1u << N) - 1u;
+    int fixed[32];
+    for (int r = 0; r < 32; ++r) fixed[r] = -1;
+    bool conflict = false;
+    for (int i = 0; i < k; ++i)
+        if (q[i].row < 0 || q[i].row >= N || q[i].col < 0 || q[i].col >= N) return NQ_EINVAL;
+    for (int i = 0; i < k; ++i) {
+        if (fixed[q[i].row] >= 0 && fixed[q[i].row] != q[i].col) conflict = true;
+        fixed[q[i].row] = q[i].col;
+    }
+    uint32_t allowed[32] = {0};
+    for (int r = 0; r < N; ++r) allowed[r] = fixed[r] >= 0 ? (1u << fixed[r]) : last;
+    for (int r0 = 0; r0 < N; ++r0) {
+        if (fixed[r0] < 0) continue;
+        const int c0 = fixed[r0];
+        for (int r = 0; r < N; ++r) {
+            if (r == r0) continue;
+            const int dr = r > r0 ? r - r0 : r0 - r;
+            uint32_t att = 1u << c0;
+            if (c0 + dr < N) att |= 1u << (c0 + dr);
+            if (c0 - dr >= 0) att |= 1u << (c0 - dr);
+            allowed[r] &= ~att;
+            if (fixed[r] >= 0 && !allowed[r]) conflict = true;  // listed queens attack
+        }
+    }
+    if (conflict) {
+        *count_out = 0;
+        return NQ_OK;
+    }
+    const int d = nq_default_depth(N);
+    std::vector<nq_prefix> pre;
+    CWalker w{N, d, last, allowed, &pre};
+    w.rec(0, 0, 0, 0);
+    if (pre.empty()) {
+        *count_out = 0;
+        return NQ_OK;
+    }
+    CallCtx ctx;
+    int rc = ctx.init();
+    if (rc) return rc;
+    nq_prefix *d_pre = nullptr;
+    uint64_t *d_tot = nullptr;
+    if ((rc = ctx.alloc(&d_pre, pre.size() * sizeof(nq_prefix)))) return rc;
+    if ((rc = ctx.alloc(&d_tot, 32 * sizeof(uint64_t)))) return rc;
+    rc = cuda_rc(cudaMemcpyAsync(d_pre, pre.data(), pre.size() * sizeof(nq_prefix),
+                                 cudaMemcpyHostToDevice, ctx.s));
+    if (!rc) rc = cuda_rc(cudaMemsetAsync(d_tot, 0, 32 * sizeof(uint64_t), ctx.s));
+    if (!rc)
+        rc = enqueue_search(d_pre, pre.size(), N, d, N, nullptr, nullptr, d_tot, nullptr,
+                            allowed, ctx.s, nullptr);
+    uint64_t tot = 0;
+    if (!rc)
+        rc = cuda_rc(cudaMemcpyAsync(&tot, d_tot + N, sizeof(uint64_t), cudaMemcpyDeviceToHost,
+                                     ctx.s));
+    if (cudaStreamSynchronize(ctx.s) != cudaSuccess) return NQ_ECUDA;
+    if (rc) return rc;
+    const int st = take_device_status();
+    if (st) return st;
+    *count_out = tot;
+    return NQ_OK;
+}

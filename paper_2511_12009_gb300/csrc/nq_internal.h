@@ -1,0 +1,58 @@
+// nq_internal.h -- declarations shared by the libnq translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "nq.h"
+
+namespace nqi {
+
+// Arguments of one search launch (device pointers unless noted).
+struct SearchArgs {
+    const nq_prefix *pre;          // [n] subproblems
+    uint64_t n;                    // number of subproblems
+    uint64_t *counts;              // [n] optional: solutions per subproblem
+    uint64_t *nodes;               // [n] optional (diagnostic build): nodes per subproblem
+    uint64_t *totals;              // [32] optional: totals[N] += weight * solutions
+    unsigned long long *cursor;    // work cursor (scratch, zeroed before the launch)
+    int expect_n;                  // 0: any board size; else every record must have this N
+    int min_d;                     // records with fewer rows placed are rejected (NQ_ESTACK)
+    int slots;                     // stack slots (16-byte frames) per thread
+    int order;                     // 1: claim the last index first
+    // Constrained mode only (partial-board queries): the columns each row may
+    // take; rows >= N and entry 31 must be 0.
+    uint32_t allowed[32];
+};
+
+// Constrained mode packs the row index of a frame into bits 27..31 of cols.
+constexpr int kRowShift = 27;
+constexpr int kMaxConstrainedN = 26;
+
+// A resolved launch shape.
+struct Plan {
+    int layout;     // NQ_LAYOUT_PAPER / NQ_LAYOUT_REG
+    int block;      // threads per block
+    int grid;       // blocks
+    int slots;      // frames per thread
+    size_t smem;    // dynamic shared memory per block, bytes
+    int sms;        // multiprocessors of the device
+};
+
+// Stack slots a layout needs for prefixes of depth >= min_d on boards <= max_n
+// (one sentinel frame included).
+int slots_needed(int layout, int max_n, int min_d);
+
+// Resolve cfg (may be NULL) into a launch shape for the current device.
+int make_plan(int max_n, int min_d, bool diag, bool constrained, const nq_config *cfg, Plan *plan);
+
+// Enqueue the search kernel. Returns NQ_OK or NQ_ECUDA.
+int launch_search(const SearchArgs &a, const Plan &p, bool diag, bool constrained, cudaStream_t s);
+
+// Read and clear the device-wide status word of the current device (synchronous).
+int take_device_status();
+
+// Host enumeration helpers (prefix.cpp).
+uint32_t meta_of(int weight, int n, int d);
+
+}  // namespace nqi

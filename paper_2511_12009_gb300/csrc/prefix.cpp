@@ -1,0 +1,222 @@
+// prefix.cpp -- host-side subproblem generation.
+//
+// The subproblems are the Somers states (cols, ld, rd) after queens were
+// pre-placed in rows 0..d-1 (Section 2: Algorithm 1 run to depth k, emitting
+// (cur, left, right) triplets), with the symmetry reduction of Section 1:
+// row 0 takes only the left half of the columns (each such subtree stands for
+// itself and its mirror image, weight 2); for odd N the centre column of row 0
+// is also taken, with the row-1 queen restricted to the left of the three
+// columns the centre queen blocks (N/2 - 1 positions, weight 2). Order:
+// depth-first, lowest column first at every row.
+#include <algorithm>
+#include <atomic>
+#include <cstring>
+#include <thread>
+#include <vector>
+
+#include "nq_internal.h"
+
+namespace nqi {
+
+uint32_t meta_of(int weight, int n, int d) { return NQ_META(weight, n, d, 0); }
+
+namespace {
+
+inline uint32_t low_bit(uint32_t v) { return v & (0u - v); }
+inline uint32_t mask_n(int n) { return n >= 32 ? ~0u : ((1u << n) - 1u); }
+
+// Columns row `row` may take in the symmetric prefix set.
+inline uint32_t row_allowed(int n, int d, int row, uint32_t col0) {
+    const int m = n / 2;
+    if (row == 0) return (n & 1) ? mask_n(m + 1) : mask_n(m);
+    if (row == 1 && (n & 1) && col0 == (1u << m) && d >= 2) return m >= 2 ? mask_n(m - 1) : 0u;
+    return ~0u;
+}
+
+inline int weight_of(int n, int d, uint32_t col0) {
+    if (d == 0) return 1;
+    if ((n & 1) && d == 1 && col0 == (1u << (n / 2))) return 1;
+    return 2;
+}
+
+struct Walker {
+    int n, d;          // board size, target depth
+    uint32_t last;
+    bool symmetric;    // apply the row-0 / row-1 rules (rows below `start` only)
+    int fixed_w;       // weight for descendants (when !symmetric)
+    nq_prefix *out;
+    uint64_t cap;
+    uint64_t count;
+
+    void emit(uint32_t cols, uint32_t ld, uint32_t rd, uint32_t col0) {
+        if (out && count < cap) {
+            const int w = symmetric ? weight_of(n, d, col0) : fixed_w;
+            out[count] = nq_prefix{cols, ld & last, rd, meta_of(w, n, d)};
+        }
+        ++count;
+    }
+
+    void rec(int row, uint32_t cols, uint32_t ld, uint32_t rd, uint32_t col0) {
+        if (row == d) {
+            emit(cols, ld, rd, col0);
+            return;
+        }
+        uint32_t av = last & ~(cols | ld | rd);
+        if (symmetric) av &= row_allowed(n, d, row, col0);
+        if (row + 1 == d && (!out || count >= cap)) {  // counting only: no need to visit leaves
+            count += (uint64_t)__builtin_popcount(av);
+            return;
+        }
+        while (av) {
+            const uint32_t p = low_bit(av);
+            av ^= p;
+            rec(row + 1, cols | p, ((ld | p) << 1) & last, (rd | p) >> 1, row == 0 ? p : col0);
+        }
+    }
+};
+
+// Depth-t nodes of the symmetric tree (their Somers state and row-0 column).
+struct Node {
+    uint32_t cols, ld, rd, col0;
+};
+
+void collect(int n, int d, int t, int row, uint32_t cols, uint32_t ld, uint32_t rd, uint32_t col0,
+             std::vector<Node> &v) {
+    const uint32_t last = mask_n(n);
+    if (row == t) {
+        v.push_back(Node{cols, ld, rd, col0});
+        return;
+    }
+    uint32_t av = last & ~(cols | ld | rd) & row_allowed(n, d, row, col0);
+    while (av) {
+        const uint32_t p = low_bit(av);
+        av ^= p;
+        collect(n, d, t, row + 1, cols | p, ((ld | p) << 1) & last, (rd | p) >> 1,
+                row == 0 ? p : col0, v);
+    }
+}
+
+// Number of depth-d prefixes below a depth-`row` node (symmetric rules apply).
+uint64_t count_below(int n, int d, int row, uint32_t cols, uint32_t ld, uint32_t rd,
+                     uint32_t col0) {
+    Walker w{n, d, mask_n(n), true, 0, nullptr, 0, 0};
+    w.rec(row, cols, ld, rd, col0);
+    return w.count;
+}
+
+// Walk to the `want`-th depth-d prefix below a node; returns true when found.
+bool find_below(int n, int d, int row, uint32_t cols, uint32_t ld, uint32_t rd, uint32_t col0,
+                uint64_t &want, nq_prefix *out) {
+    const uint32_t last = mask_n(n);
+    if (row == d) {
+        if (want == 0) {
+            *out = nq_prefix{cols, ld & last, rd, meta_of(weight_of(n, d, col0), n, d)};
+            return true;
+        }
+        --want;
+        return false;
+    }
+    uint32_t av = last & ~(cols | ld | rd) & row_allowed(n, d, row, col0);
+    while (av) {
+        const uint32_t p = low_bit(av);
+        av ^= p;
+        const uint32_t nc = cols | p, nl = ((ld | p) << 1) & last, nr = (rd | p) >> 1;
+        const uint32_t n0 = row == 0 ? p : col0;
+        if (row + 1 < d) {
+            const uint64_t below = count_below(n, d, row + 1, nc, nl, nr, n0);
+            if (want >= below) {
+                want -= below;
+                continue;
+            }
+        }
+        if (find_below(n, d, row + 1, nc, nl, nr, n0, want, out)) return true;
+    }
+    return false;
+}
+
+unsigned worker_count() {
+    const unsigned h = std::thread::hardware_concurrency();
+    return h ? std::min(h, 64u) : 1u;
+}
+
+}  // namespace
+}  // namespace nqi
+
+using namespace nqi;
+
+extern "C" int nq_default_depth(int N) {
+    if (N < 1 || N > NQ_MAX_N) return NQ_EINVAL;
+    int d;
+    if (N <= 12) d = 3;
+    else if (N <= 14) d = 4;
+    else if (N <= 17) d = 5;
+    else if (N <= 22) d = 6;
+    else d = 7;
+    return std::max(0, std::min(d, N - 2));
+}
+
+extern "C" int nq_enumerate_prefixes(int N, int d, nq_prefix *out, uint64_t cap, uint64_t *n_out) {
+    if (N < 1 || N > NQ_MAX_N || d < 0 || d > N || !n_out) return NQ_EINVAL;
+    Walker w{N, d, mask_n(N), true, 0, out, out ? cap : 0, 0};
+    w.rec(0, 0, 0, 0, 0);
+    *n_out = w.count;
+    return (out && w.count > cap) ? NQ_EOVERFLOW : NQ_OK;
+}
+
+extern "C" int nq_descendants(const nq_prefix *parent, int rows, nq_prefix *out, uint64_t cap,
+                              uint64_t *n_out) {
+    if (!parent || !n_out || rows < 0) return NQ_EINVAL;
+    const int n = (int)NQ_META_N(parent->meta), d = (int)NQ_META_D(parent->meta);
+    const int w = (int)NQ_META_WEIGHT(parent->meta);
+    if (n < 1 || d + rows > n || (w != 1 && w != 2)) return NQ_EINVAL;
+    const uint32_t last = mask_n(n);
+    if ((parent->cols & ~last) || __builtin_popcount(parent->cols) != d) return NQ_EINVAL;
+    Walker wk{n, d + rows, last, false, w, out, out ? cap : 0, 0};
+    wk.rec(d, parent->cols, parent->ld & last, parent->rd & last, 0);
+    *n_out = wk.count;
+    return (out && wk.count > cap) ? NQ_EOVERFLOW : NQ_OK;
+}
+
+extern "C" int nq_prefixes_at_ranks(int N, int d, const uint64_t *ranks, uint64_t k,
+                                    nq_prefix *out) {
+    if (N < 1 || N > NQ_MAX_N || d < 0 || d > N || (k && (!ranks || !out))) return NQ_EINVAL;
+    // Step 1: depth-t nodes and the number of depth-d prefixes below each.
+    const int t = d > 3 ? d - 3 : 0;
+    std::vector<Node> nodes;
+    collect(N, d, t, 0, 0, 0, 0, 0, nodes);
+    std::vector<uint64_t> first(nodes.size() + 1, 0);
+    std::atomic<size_t> next{0};
+    auto work = [&]() {
+        for (;;) {
+            const size_t i = next.fetch_add(1);
+            if (i >= nodes.size()) break;
+            const Node &v = nodes[i];
+            first[i + 1] = count_below(N, d, t, v.cols, v.ld, v.rd, v.col0);
+        }
+    };
+    std::vector<std::thread> th;
+    const unsigned nw = nodes.size() > 4096 ? worker_count() : 1u;
+    for (unsigned i = 1; i < nw; ++i) th.emplace_back(work);
+    work();
+    for (auto &x : th) x.join();
+    for (size_t i = 0; i < nodes.size(); ++i) first[i + 1] += first[i];
+    // Step 2: locate each rank.
+    int rc = NQ_OK;
+    for (uint64_t s = 0; s < k; ++s) {
+        const uint64_t rank = ranks[s];
+        if (nodes.empty() || rank >= first.back()) {
+            out[s] = nq_prefix{0, 0, 0, 0};
+            rc = NQ_EINVAL;
+            continue;
+        }
+        const size_t j = (size_t)(std::upper_bound(first.begin(), first.end(), rank) -
+                                  first.begin()) - 1;
+        uint64_t want = rank - first[j];
+        const Node &v = nodes[j];
+        if (!find_below(N, d, t, v.cols, v.ld, v.rd, v.col0, want, &out[s])) {
+            out[s] = nq_prefix{0, 0, 0, 0};
+            rc = NQ_EINVAL;
+        }
+    }
+    return rc;
+}

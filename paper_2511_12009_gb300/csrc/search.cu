@@ -1,0 +1,411 @@
+// search.cu -- the persistent depth-first search kernel (sm_103a).
+//
+// What one thread does (Section 2, Algorithm 2, with the last-row rule of
+// Section 3.2.3 / Algorithm 3): it takes a subproblem (the Somers state after
+// rows 0..d-1 were pre-placed), walks that subtree depth-first with an explicit
+// stack of 16-byte frames {cols, ld, rd, avail} in shared memory, picks the
+// next column as the lowest set bit of avail (p = avail & -avail), and, once
+// rows 0..N-2 hold queens, adds whether row N-1 still has a free column instead
+// of pushing another frame.
+//
+// GB300 design (what differs from the paper's kernel, which gives each thread
+// one fixed subproblem of a static grid):
+//   - persistent grid, SMs x resident blocks; every lane claims its next
+//     subproblem from a global cursor with one warp-aggregated atomicAdd as
+//     soon as its own subtree is done, so uneven subtrees balance themselves;
+//   - per-thread stacks interleaved by thread: frame k of thread t lives at
+//     byte (k * blockDim + t) * 16, so the 8 lanes of each 128-byte phase of a
+//     warp hit 8 distinct 16-byte bank groups at any mix of depths (the paper's
+//     conflict-free idea, Section 3.1, in its int4 form);
+//   - columns >= N are pre-set in cols, which makes the next-row mask a single
+//     three-input NOR and the kernel independent of N: subproblems of several
+//     board sizes can share one launch (batched mode);
+//   - the loop body is branch-free: a sentinel frame at the bottom of every
+//     stack keeps a finished lane harmlessly "searching" a board with no free
+//     column until the next bookkeeping point, which comes every kChunk steps
+//     (kChunk < 32 keeps the sentinel's 32 candidate bits from running out);
+//   - uint64 solution counts per subproblem; weighted totals reduced per warp
+//     with shuffles, one atomicAdd per warp and board size.
+//
+// Constrained mode (partial-board queries, the serving extension; not in the
+// paper): every row r has a mask allowed[r] of the columns it may take (one
+// column for a row with a given queen; the cells the given queens attack
+// removed elsewhere), the frame's row index rides in bits 27..31 of cols, and
+// the next-row mask is additionally ANDed with allowed[row].
+#include <cstdio>
+
+#include "nq_internal.h"
+
+namespace nqi {
+
+__device__ int g_status;  // first error any launch recorded on this device
+
+namespace {
+
+constexpr uint64_t kNone = ~0ull;
+constexpr int kChunk = 16;
+static_assert(kChunk < 32, "the sentinel frame holds 32 idle steps");
+constexpr uint32_t kRowInc = 1u << kRowShift;
+// Constrained-mode sentinel: row field 30, so the child is row 31 whose allowed
+// mask is 0 -- no push, no count; its candidate bits stay below the row field,
+// so cols never wraps.
+constexpr uint32_t kSentinelC = (30u << kRowShift) | (kRowInc - 1u);
+constexpr uint32_t kSentinelAvC = kRowInc - 1u;
+static_assert(kChunk < kRowShift, "constrained sentinel holds 27 idle steps");
+
+extern __shared__ __align__(16) unsigned char nq_smem[];
+
+__device__ __forceinline__ void record_error(int code) { atomicCAS(&g_status, 0, code); }
+
+__device__ __forceinline__ uint4 lds4(uint32_t off) {
+    return *reinterpret_cast<const uint4 *>(nq_smem + off);
+}
+__device__ __forceinline__ uint32_t lds1(uint32_t off) {
+    return *reinterpret_cast<const uint32_t *>(nq_smem + off);
+}
+__device__ __forceinline__ void sts4(uint32_t off, uint4 v) {
+    *reinterpret_cast<uint4 *>(nq_smem + off) = v;
+}
+__device__ __forceinline__ void sts1(uint32_t off, uint32_t v) {
+    *reinterpret_cast<uint32_t *>(nq_smem + off) = v;
+}
+
+// True when the child state c2 has exactly one free column left (bits >= N
+// are pre-set), i.e. queens now sit in rows 0..N-2: Algorithm 3's
+// popc(cur) == N-1 test.
+__device__ __forceinline__ bool one_free(uint32_t c2) { return (c2 | (c2 + 1u)) == ~0u; }
+
+// Per-lane constants of a step.
+struct Lane {
+    uint32_t stride;   // bytes between a thread's consecutive frames
+    uint32_t base;     // byte offset of this thread's slot 0 (the sentinel)
+    uint32_t limit;    // one past this thread's last slot
+    uint32_t table;    // constrained mode: byte offset of allowed[]
+    uint32_t thr;      // constrained mode: (N-1) << 27, the last-row threshold
+};
+
+// One step, layout REG: the top frame (c, l, r, av) lives in registers, the
+// stack holds only ancestors that still have untried columns.
+template <bool DIAG, bool CONSTR>
+__device__ __forceinline__ void step_reg(uint32_t &c, uint32_t &l, uint32_t &r, uint32_t &av,
+                                         uint32_t &top, const Lane &k, uint32_t &s32,
+                                         uint32_t &n32) {
+    const uint32_t p = av & (0u - av);  // lowest free column (Algorithm 2, line 10)
+    const uint32_t ar = av ^ p;         // the columns still to try here
+    uint32_t c2, a2;
+    bool lastrow;
+    const uint32_t l2 = (l | p) << 1;
+    const uint32_t r2 = (r | p) >> 1;
+    if (CONSTR) {
+        c2 = (c | p) + kRowInc;
+        a2 = ~(c2 | l2 | r2) & lds1(k.table + ((c2 >> kRowShift) << 2));
+        lastrow = c2 >= k.thr;
+    } else {
+        c2 = c | p;
+        a2 = ~(c2 | l2 | r2);  // free columns of the next row
+        lastrow = one_free(c2);
+    }
+    const bool live = a2 != 0u;
+    s32 += (lastrow && live) ? 1u : 0u;  // Algorithm 3: count instead of pushing
+    if (DIAG) n32 += (CONSTR ? (c >> kRowShift) < 30u : c != ~0u) ? 1u : 0u;
+    const bool push = !lastrow && live;
+    if (push && ar != 0u) {
+        if (!DIAG || top < k.limit) {
+            sts4(top, make_uint4(c, l, r, ar));
+            top += k.stride;
+        } else {
+            record_error(NQ_ESTACK);
+        }
+    }
+    if (!push && ar == 0u) {
+        if (!DIAG || top > k.base) {
+            top -= k.stride;
+            const uint4 f = lds4(top);
+            c = f.x; l = f.y; r = f.z; av = f.w;
+        } else {
+            record_error(NQ_ESTACK);
+            c = CONSTR ? kSentinelC : ~0u;
+            l = r = ~0u;
+            av = CONSTR ? kSentinelAvC : ~0u;
+        }
+    } else if (push) {
+        c = c2; l = l2; r = r2; av = a2;
+    } else {
+        av = ar;
+    }
+}
+
+// One step, layout PAPER: Algorithm 2 with Algorithm 3 as printed -- read the
+// top frame, take its lowest column, write back the rest, pop the frame when
+// nothing is left, push the child when it is not the last row and not dead.
+template <bool DIAG>
+__device__ __forceinline__ void step_paper(uint32_t &top, const Lane &k, uint32_t &s32,
+                                           uint32_t &n32) {
+    if (DIAG && top <= k.base) {
+        record_error(NQ_ESTACK);
+        return;
+    }
+    const uint4 f = lds4(top - k.stride);
+    const uint32_t p = f.w & (0u - f.w);
+    const uint32_t ar = f.w ^ p;
+    sts1(top - k.stride + 12u, ar);
+    if (ar == 0u) top -= k.stride;
+    const uint32_t c2 = f.x | p;
+    const uint32_t l2 = (f.y | p) << 1;
+    const uint32_t r2 = (f.z | p) >> 1;
+    const uint32_t a2 = ~(c2 | l2 | r2);
+    const bool lastrow = one_free(c2);
+    const bool live = a2 != 0u;
+    s32 += (lastrow && live) ? 1u : 0u;
+    if (DIAG) n32 += (f.x != ~0u) ? 1u : 0u;
+    if (!lastrow && live) {
+        if (!DIAG || top < k.limit) {
+            sts4(top, make_uint4(c2, l2, r2, a2));
+            top += k.stride;
+        } else {
+            record_error(NQ_ESTACK);
+        }
+    }
+}
+
+template <int LAYOUT, bool DIAG, bool CONSTR>
+__global__ void __launch_bounds__(1024, 1) search_kernel(const SearchArgs a) {
+    constexpr bool kReg = LAYOUT == NQ_LAYOUT_REG;
+    static_assert(kReg || !CONSTR, "constrained mode uses the REG layout");
+    Lane k;
+    k.stride = blockDim.x * 16u;
+    k.base = threadIdx.x * 16u;
+    k.limit = k.base + (uint32_t)a.slots * k.stride;
+    k.table = (uint32_t)a.slots * k.stride;
+    k.thr = 0;
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned lt_mask = (1u << lane) - 1u;
+    if (CONSTR) {
+        if (threadIdx.x < 32) sts1(k.table + threadIdx.x * 4u, a.allowed[threadIdx.x]);
+        __syncthreads();
+    }
+    const uint32_t sent_c = CONSTR ? kSentinelC : ~0u;
+    const uint32_t sent_av = CONSTR ? kSentinelAvC : ~0u;
+
+    uint32_t c = sent_c, l = ~0u, r = ~0u, av = sent_av;  // REG: the top frame
+    uint32_t top = k.base;                            // byte offset: next free slot
+    // Slot 0 of every stack holds the sentinel frame. REG pops it when a
+    // subproblem is exhausted (the lane then idles on it until the next
+    // bookkeeping point); PAPER keeps it as the top frame while idle.
+    sts4(k.base, make_uint4(sent_c, ~0u, ~0u, sent_av));
+    if (!kReg) top = k.base + k.stride;
+    const uint32_t idle_top = kReg ? k.base : k.base + k.stride;
+
+    uint64_t idx = kNone;   // subproblem in progress
+    uint32_t wt = 0, pn = 0;
+    uint64_t sol = 0, nod = 0;
+    uint64_t wsum = 0;      // weighted solutions not yet in totals[wsum_n]
+    uint32_t wsum_n = 0;
+    bool exhausted = false;
+
+    auto finish = [&](uint64_t i, uint64_t s, uint64_t nodes_below, uint32_t w, uint32_t n) {
+        if (a.counts) a.counts[i] = s;
+        if (DIAG && a.nodes) a.nodes[i] = nodes_below;
+        if (a.totals && s) {
+            if (n != wsum_n && wsum != 0) {
+                atomicAdd(reinterpret_cast<unsigned long long *>(&a.totals[wsum_n]),
+                          (unsigned long long)wsum);
+                wsum = 0;
+            }
+            wsum_n = n;
+            wsum += (uint64_t)w * s;
+        }
+    };
+
+    for (;;) {
+        const bool idle = top == idle_top;
+        if (idle) {
+            if (idx != kNone) {
+                finish(idx, sol, nod + sol, wt, pn);
+                idx = kNone;
+            }
+            if (kReg) {
+                c = sent_c;
+                l = r = ~0u;
+                av = sent_av;
+            } else {
+                sts1(k.base + 12u, ~0u);
+            }
+        }
+        bool need = idle && !exhausted;
+        unsigned need_mask = __ballot_sync(~0u, need);
+        while (need_mask) {
+            const int leader = __ffs(need_mask) - 1;
+            unsigned long long first = 0;
+            if ((int)lane == leader)
+                first = atomicAdd(a.cursor, (unsigned long long)__popc(need_mask));
+            first = __shfl_sync(~0u, first, leader);
+            if (need) {
+                const uint64_t my = first + (uint64_t)__popc(need_mask & lt_mask);
+                if (my >= a.n) {
+                    exhausted = true;
+                    need = false;
+                } else {
+                    const uint64_t pi = a.order ? a.n - 1 - my : my;
+                    const uint4 P = __ldg(reinterpret_cast<const uint4 *>(a.pre) + pi);
+                    const uint32_t n = (P.w >> 2) & 31u, d = (P.w >> 7) & 31u, w = P.w & 3u;
+                    const uint32_t last = (n >= 1u) ? (0xFFFFFFFFu >> (32u - n)) : 0u;
+                    const bool ok = n >= 1u && (a.expect_n == 0 || (int)n == a.expect_n) &&
+                                    (w == 1u || w == 2u) && d <= n && (P.x & ~last) == 0u &&
+                                    (uint32_t)__popc(P.x) == d &&
+                                    (!CONSTR || n <= (uint32_t)kMaxConstrainedN);
+                    const int need_slots = kReg ? (int)n - 1 - (int)d : (int)n - (int)d;
+                    if (!ok) {
+                        record_error(NQ_EINVAL);
+                        finish(pi, 0, 0, 0, 0);
+                    } else if (d + 1u < n && need_slots > a.slots) {
+                        record_error(NQ_ESTACK);
+                        finish(pi, 0, 0, 0, 0);
+                    } else {
+                        const uint32_t l0 = P.y;
+                        const uint32_t r0 = P.z & last;
+                        uint32_t c0, a0;
+                        if (CONSTR) {
+                            c0 = P.x | (d << kRowShift);
+                            a0 = ~(c0 | l0 | r0) & lds1(k.table + (d << 2)) & last;
+                        } else {
+                            c0 = P.x | ~last;
+                            a0 = ~(c0 | l0 | r0);
+                        }
+                        if (d == n) {
+                            finish(pi, 1, 0, w, n);  // the prefix is a solution
+                        } else if (d + 1u == n || a0 == 0u) {
+                            const uint64_t s = (uint64_t)__popc(a0);  // last row or dead end
+                            finish(pi, s, s, w, n);
+                        } else {
+                            idx = pi; wt = w; pn = n; sol = 0; nod = 0;
+                            k.thr = (n - 1u) << kRowShift;
+                            if (kReg) {
+                                c = c0; l = l0; r = r0; av = a0;
+                                top = k.base + k.stride;  // above the sentinel
+                            } else {
+                                sts4(k.base + k.stride, make_uint4(c0, l0, r0, a0));
+                                top = k.base + 2u * k.stride;
+                            }
+                            need = false;
+                        }
+                    }
+                }
+            }
+            need_mask = __ballot_sync(~0u, need);
+        }
+        if (__all_sync(~0u, exhausted && idx == kNone)) break;
+
+        uint32_t s32 = 0, n32 = 0;
+#pragma unroll
+        for (int j = 0; j < kChunk; ++j) {
+            if (kReg)
+                step_reg<DIAG, CONSTR>(c, l, r, av, top, k, s32, n32);
+            else
+                step_paper<DIAG>(top, k, s32, n32);
+        }
+        sol += s32;
+        if (DIAG) nod += n32;
+    }
+
+    if (a.totals) {
+        const unsigned has = __ballot_sync(~0u, wsum != 0);
+        if (has) {
+            const uint32_t n0 = __shfl_sync(~0u, wsum_n, __ffs(has) - 1);
+            if (__all_sync(~0u, wsum == 0 || wsum_n == n0)) {
+                uint64_t v = wsum;
+                for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(~0u, v, o);
+                if (lane == 0)
+                    atomicAdd(reinterpret_cast<unsigned long long *>(&a.totals[n0]),
+                              (unsigned long long)v);
+            } else if (wsum) {
+                atomicAdd(reinterpret_cast<unsigned long long *>(&a.totals[wsum_n]),
+                          (unsigned long long)wsum);
+            }
+        }
+    }
+}
+
+template <int LAYOUT, bool DIAG, bool CONSTR>
+void *kernel_ptr() {
+    return reinterpret_cast<void *>(&search_kernel<LAYOUT, DIAG, CONSTR>);
+}
+
+void *pick_kernel(int layout, bool diag, bool constrained) {
+    if (constrained)
+        return diag ? kernel_ptr<NQ_LAYOUT_REG, true, true>()
+                    : kernel_ptr<NQ_LAYOUT_REG, false, true>();
+    if (layout == NQ_LAYOUT_PAPER)
+        return diag ? kernel_ptr<NQ_LAYOUT_PAPER, true, false>()
+                    : kernel_ptr<NQ_LAYOUT_PAPER, false, false>();
+    return diag ? kernel_ptr<NQ_LAYOUT_REG, true, false>()
+                : kernel_ptr<NQ_LAYOUT_REG, false, false>();
+}
+
+}  // namespace
+
+int slots_needed(int layout, int max_n, int min_d) {
+    int s = (layout == NQ_LAYOUT_PAPER) ? max_n - min_d : max_n - 1 - min_d;
+    return s < 1 ? 1 : s;
+}
+
+int make_plan(int max_n, int min_d, bool diag, bool constrained, const nq_config *cfg,
+              Plan *plan) {
+    if (max_n < 1 || max_n > NQ_MAX_N || min_d < 0 || min_d > max_n) return NQ_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return NQ_ECUDA;
+    int sms = 0, max_smem = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+            cudaSuccess)
+        return NQ_ECUDA;
+    Plan p{};
+    p.layout = (cfg && cfg->layout) ? cfg->layout : NQ_LAYOUT_REG;
+    if (p.layout != NQ_LAYOUT_PAPER && p.layout != NQ_LAYOUT_REG) return NQ_EINVAL;
+    if (constrained) p.layout = NQ_LAYOUT_REG;
+    p.block = (cfg && cfg->block) ? cfg->block : 256;
+    if (p.block < 32 || p.block > 1024 || p.block % 32) return NQ_EINVAL;
+    p.slots = slots_needed(p.layout, max_n, min_d);
+    const size_t per_thread = (size_t)p.slots * 16u;
+    const size_t extra = constrained ? 32u * 4u : 0u;
+    if ((size_t)p.block * per_thread + extra > (size_t)max_smem) {
+        int fit = (int)(((size_t)max_smem - extra) / per_thread) / 32 * 32;
+        if (fit < 32) return NQ_ESTACK;
+        p.block = fit;
+    }
+    p.smem = (size_t)p.block * per_thread + extra;
+    void *k = pick_kernel(p.layout, diag, constrained);
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem) !=
+        cudaSuccess)
+        return NQ_ECUDA;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, p.block, p.smem) != cudaSuccess)
+        return NQ_ECUDA;
+    if (nb < 1) return NQ_ESTACK;
+    if (cfg && cfg->blocks_per_sm > 0 && cfg->blocks_per_sm < nb) nb = cfg->blocks_per_sm;
+    p.sms = sms;
+    p.grid = sms * nb;
+    *plan = p;
+    return NQ_OK;
+}
+
+int launch_search(const SearchArgs &a, const Plan &p, bool diag, bool constrained,
+                  cudaStream_t s) {
+    if (a.n == 0) return NQ_OK;
+    void *k = pick_kernel(p.layout, diag, constrained);
+    SearchArgs args = a;
+    void *params[] = {&args};
+    const cudaError_t e = cudaLaunchKernel(k, dim3(p.grid), dim3(p.block), params, p.smem, s);
+    return e == cudaSuccess ? NQ_OK : NQ_ECUDA;
+}
+
+int take_device_status() {
+    int v = 0;
+    const int zero = 0;
+    if (cudaMemcpyFromSymbol(&v, g_status, sizeof(int)) != cudaSuccess) return NQ_ECUDA;
+    if (v != 0 && cudaMemcpyToSymbol(g_status, &zero, sizeof(int)) != cudaSuccess)
+        return NQ_ECUDA;
+    return v;
+}
+
+}  // namespace nqi

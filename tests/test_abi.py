@@ -1,0 +1,121 @@
+"""CPU tests of the C ABI: the library builds for sm_103a, loads, exports every
+entry point include/nq.h declares, and its host-side prefix generation equals
+the oracle's. No call here launches a kernel."""
+import ctypes
+import json
+import os
+
+import numpy as np
+import pytest
+
+import synth_inputs
+from paper_2511_12009_gb300 import nq
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def to_state(n, cols_list):
+    """Somers state (cols, ld, rd) of row d after queens at (r, cols_list[r]), r < d,
+    from the board geometry: a queen at (r, c) attacks row d at c + (d - r) along one
+    diagonal and c - (d - r) along the other."""
+    d = len(cols_list)
+    cols = sum(1 << int(c) for c in cols_list)
+    ld = sum(1 << (int(c) + d - r) for r, c in enumerate(cols_list) if int(c) + d - r < n)
+    rd = sum(1 << (int(c) - d + r) for r, c in enumerate(cols_list) if int(c) - d + r >= 0)
+    return cols, ld, rd
+
+
+def test_library_exports_every_declared_symbol():
+    lib = nq.lib()
+    syms = nq.header_symbols()
+    assert len(syms) >= 10
+    missing = [s for s in syms if not hasattr(lib, s)]
+    assert not missing, missing
+
+
+def test_strerror_names_every_code():
+    for code in range(0, -8, -1):
+        assert nq.strerror(code) and "unknown" not in nq.strerror(code)
+    assert "unknown" in nq.strerror(-99)
+
+
+@pytest.mark.parametrize("n,d", [(1, 0), (1, 1), (2, 2), (3, 2), (4, 2), (5, 1), (5, 2), (8, 3),
+                                 (9, 4), (11, 5), (12, 0), (13, 3), (14, 3), (16, 5), (17, 4)])
+def test_enumeration_equals_oracle(orc, n, d):
+    got = nq.enumerate_prefixes(n, d)
+    cols, w = orc.prefixes(n, d)
+    assert len(got) == len(cols)
+    for rec, q, wt in zip(got, cols, w):
+        c, l, r = to_state(n, q)
+        assert (int(rec["cols"]), int(rec["ld"]), int(rec["rd"])) == (c, l, r)
+        meta = int(rec["meta"])
+        assert meta & 3 == wt and (meta >> 2) & 31 == n and (meta >> 7) & 31 == d
+        assert meta >> 12 == 0
+
+
+@pytest.mark.parametrize("n,d", [(18, 5), (18, 6), (21, 5), (22, 5), (22, 6)])
+def test_prefix_counts_equal_oracle(orc, n, d):
+    assert nq.prefix_count(n, d) == orc.prefix_count(n, d)
+
+
+def test_prefix_count_paper_n27():
+    v = json.load(open(os.path.join(GOLDEN, "paper_values.json")))["n27_subproblems"]
+    assert nq.prefix_count(v["n"], v["d"]) == v["value"]
+
+
+@pytest.mark.parametrize("n,d", [(10, 2), (12, 5), (13, 6), (16, 4)])
+def test_ranks_equal_oracle(orc, n, d):
+    total = nq.prefix_count(n, d)
+    ranks = synth_inputs.sample_indices(11, total, 64) + [0, total - 1]
+    got = nq.prefixes_at_ranks(n, d, ranks)
+    want = orc.prefixes_at_ranks(n, d, ranks)
+    for rec, q in zip(got, want):
+        assert (int(rec["cols"]), int(rec["ld"]), int(rec["rd"])) == to_state(n, q)
+
+
+def test_rank_out_of_range():
+    with pytest.raises(nq.NQError) as e:
+        nq.prefixes_at_ranks(8, 3, [nq.prefix_count(8, 3)])
+    assert e.value.code == nq.NQ_EINVAL
+
+
+def test_descendants_refine_in_order():
+    n, d = 11, 3
+    parents = nq.enumerate_prefixes(n, d)
+    children = nq.enumerate_prefixes(n, d + 2)
+    joined = np.concatenate([nq.descendants(p, 2) for p in parents])
+    assert np.array_equal(joined, children)
+
+
+def test_descendants_of_root_cover_the_board():
+    # all 3-row placements of a 9x9 board, no symmetry (weight 1), by brute force
+    kids = nq.descendants(nq.enumerate_prefixes(9, 0)[0], 3)
+    brute = sum(1 for a in range(9) for b in range(9) for c in range(9)
+                if len({a, b, c}) == 3 and abs(a - b) != 1 and abs(b - c) != 1 and abs(a - c) != 2)
+    assert len(kids) == brute and all(int(k["meta"]) & 3 == 1 for k in kids)
+
+
+@pytest.mark.parametrize("args", [(0, 0), (32, 3), (8, 9), (8, -1)])
+def test_enumerate_rejects_bad_sizes(args):
+    num = ctypes.c_uint64(0)
+    assert nq.lib().nq_enumerate_prefixes(args[0], args[1], None, 0, ctypes.byref(num)) == nq.NQ_EINVAL
+
+
+def test_enumerate_cap_overflow():
+    out = np.zeros(3, dtype=nq.PREFIX_DTYPE)
+    num = ctypes.c_uint64(0)
+    rc = nq.lib().nq_enumerate_prefixes(8, 3, out.ctypes.data, 3, ctypes.byref(num))
+    assert rc == nq.NQ_EOVERFLOW and num.value == nq.prefix_count(8, 3)
+    assert np.array_equal(out, nq.enumerate_prefixes(8, 3)[:3])
+
+
+def test_total_rejects_overflowing_sizes():
+    out = ctypes.c_uint64(0)
+    assert nq.lib().nq_total(29, ctypes.byref(out)) == nq.NQ_EOVERFLOW
+    assert nq.lib().nq_total(0, ctypes.byref(out)) == nq.NQ_EINVAL
+
+
+def test_default_depth_in_range():
+    for n in range(1, 32):
+        d = nq.default_depth(n)
+        assert 0 <= d <= max(n - 2, 0)

@@ -1,0 +1,219 @@
+"""GPU parity: libnq's CUDA search against the CPU oracle, element by element.
+
+Counts are integers, so the bar is bit-exact equality for every per-prefix
+count, every per-prefix node count and every total. Inputs are the canonical
+prefix sets (seeded samples where the oracle cannot cover a whole set), on
+sizes that span many warps and blocks with ragged tails, plus the degenerate
+cases (empty batch, prefixes that already are solutions, one row left, dead
+prefixes, the whole board as one prefix).
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import synth_inputs
+from paper_2511_12009_gb300 import nq
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+Q = {int(k): v for k, v in json.load(open(os.path.join(GOLDEN, "oeis_a000170.json")))["Q"].items()}
+LAYOUTS = ["paper", "reg"]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    nq.lib()
+
+
+def u64(t):
+    return t.cpu().numpy().view(np.uint64)
+
+
+def run(pre, min_d, max_n, layout="reg", nodes=False, **cfg):
+    dp = nq.to_device(pre)
+    m = len(pre)
+    cnt = torch.full((max(m, 1),), -1, dtype=torch.int64, device="cuda")
+    nod = torch.full((max(m, 1),), -1, dtype=torch.int64, device="cuda") if nodes else None
+    tot = torch.zeros(32, dtype=torch.int64, device="cuda")
+    nq.count_ex(dp, min_d, max_n, cnt, nod, tot, nq.make_config(layout, **cfg))
+    nq.sync()
+    return u64(cnt)[:m], (u64(nod)[:m] if nodes else None), u64(tot)
+
+
+def weighted(pre, counts):
+    return int(sum(int(m & 3) * int(c) for m, c in zip(pre["meta"], counts)))
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+@pytest.mark.parametrize("n,d", [(1, 0), (1, 1), (2, 1), (3, 1), (4, 2), (5, 1), (5, 2), (6, 0),
+                                 (7, 3), (8, 0), (8, 3), (9, 2), (10, 4), (11, 3), (12, 4), (13, 5),
+                                 (14, 3), (14, 6), (15, 5), (16, 5)])
+def test_per_prefix_counts_and_nodes(orc, layout, n, d):
+    pre = nq.enumerate_prefixes(n, d)
+    cols, _ = orc.prefixes(n, d)
+    want_c, want_n = orc.count_prefixes(n, cols)
+    got_c, got_n, tot = run(pre, d, n, layout, nodes=True)
+    assert np.array_equal(got_c, want_c)
+    assert np.array_equal(got_n, want_n)
+    assert int(tot[n]) == Q[n] == weighted(pre, got_c)
+    # the production build (no node counters) gives the same counts
+    got_c2, _, tot2 = run(pre, d, n, layout)
+    assert np.array_equal(got_c2, want_c) and int(tot2[n]) == Q[n]
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+@pytest.mark.parametrize("n", [16, 17, 18])
+def test_full_board_golden(layout, n):
+    """Every one of the d=5 prefixes' counts and nodes, against arrays the oracle wrote."""
+    g = np.load(os.path.join(GOLDEN, f"oracle_n{n}_d5.npz"))
+    pre = nq.enumerate_prefixes(n, 5)
+    assert np.array_equal(pre["meta"] & 3, g["weights"])
+    got_c, got_n, tot = run(pre, 5, n, layout, nodes=True)
+    assert np.array_equal(got_c, g["counts"])
+    assert np.array_equal(got_n, g["nodes"])
+    assert int(tot[n]) == Q[n]
+    got_c2, _, tot2 = run(pre, 5, n, layout)
+    assert np.array_equal(got_c2, g["counts"]) and int(tot2[n]) == Q[n]
+
+
+@pytest.mark.parametrize("n", list(range(1, 21)))
+def test_total_public_entry(n):
+    assert nq.total(n) == Q[n]
+
+
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_launch_shapes(orc, layout):
+    """Block sizes, blocks per SM and claim order do not change any count."""
+    n, d = 13, 4
+    pre = nq.enumerate_prefixes(n, d)
+    want, _ = orc.count_prefixes(n, orc.prefixes(n, d)[0])
+    for block, bps, order in [(32, 1, 0), (64, 3, 1), (128, 0, 0), (512, 1, 1), (1024, 0, 0)]:
+        got, _, tot = run(pre, d, n, layout, block=block, blocks_per_sm=bps, order=order)
+        assert np.array_equal(got, want), (block, bps, order)
+        assert int(tot[n]) == Q[n]
+
+
+def test_sampled_prefixes_at_bench_shape(orc):
+    """N=18 at the library's default depth, in the default launch: 256 seeded
+    prefixes, each checked one by one against the oracle."""
+    n = 18
+    d = nq.default_depth(n)
+    pre = nq.enumerate_prefixes(n, d)
+    got, _, tot = run(pre, d, n, "default")
+    assert int(tot[n]) == Q[n]
+    idx = synth_inputs.sample_indices(2024, len(pre), 256)
+    cols, _ = orc.prefixes(n, d)
+    want, _ = orc.count_prefixes(n, cols[idx])
+    assert np.array_equal(got[idx], want)
+
+
+def test_mixed_board_sizes_one_launch(orc):
+    """Prefixes of N=6..14 interleaved in one launch: per-prefix counts and per-N totals."""
+    parts, want = [], []
+    for n in range(6, 15):
+        d = 3
+        parts.append(nq.enumerate_prefixes(n, d))
+        want.append(orc.count_prefixes(n, orc.prefixes(n, d)[0])[0])
+    pre = np.concatenate(parts)
+    perm = np.random.default_rng(5).permutation(len(pre))
+    got, _, tot = run(pre[perm], 3, 14)
+    assert np.array_equal(got, np.concatenate(want)[perm])
+    for n in range(6, 15):
+        assert int(tot[n]) == Q[n]
+
+
+def test_empty_batch():
+    pre = nq.enumerate_prefixes(2, 2)
+    assert len(pre) == 0
+    got, _, tot = run(pre, 2, 2)
+    assert len(got) == 0 and int(tot.sum()) == 0
+
+
+def test_degenerate_prefixes(orc):
+    """d = N (the prefixes are solutions), d = N - 1 (one row left), and
+    prefixes whose next row is already dead."""
+    for n in (6, 8, 9):
+        for d in (n, n - 1, n - 2):
+            pre = nq.enumerate_prefixes(n, d)
+            want, want_n = orc.count_prefixes(n, orc.prefixes(n, d)[0])
+            got, got_n, tot = run(pre, d, n, nodes=True)
+            assert np.array_equal(got, want) and np.array_equal(got_n, want_n)
+            assert int(tot[n]) == Q[n]
+
+
+def test_malformed_records_are_rejected():
+    pre = nq.enumerate_prefixes(10, 3).copy()
+    pre["meta"][5] = (pre["meta"][5] & ~np.uint32(3))          # weight 0
+    pre["cols"][7] |= np.uint32(1 << 12)                         # column outside the board
+    got, _, tot = run(pre[:0], 3, 10)                           # empty: nothing recorded
+    dp = nq.to_device(pre)
+    cnt = torch.full((len(pre),), -1, dtype=torch.int64, device="cuda")
+    nq.count(10, 3, dp, cnt)
+    with pytest.raises(nq.NQError) as e:
+        nq.sync()
+    assert e.value.code == nq.NQ_EINVAL
+    c = u64(cnt)
+    assert c[5] == 0 and c[7] == 0
+    nq.sync()  # the status was cleared
+
+
+def test_wrong_board_size_is_rejected():
+    pre = nq.enumerate_prefixes(10, 3)
+    dp = nq.to_device(pre)
+    cnt = torch.zeros(len(pre), dtype=torch.int64, device="cuda")
+    nq.count(11, 3, dp, cnt)
+    with pytest.raises(nq.NQError) as e:
+        nq.sync()
+    assert e.value.code == nq.NQ_EINVAL and int(cnt.abs().sum()) == 0
+
+
+def test_prefix_shallower_than_declared_is_rejected():
+    pre = nq.enumerate_prefixes(12, 2)
+    dp = nq.to_device(pre)
+    cnt = torch.zeros(len(pre), dtype=torch.int64, device="cuda")
+    nq.count(12, 5, dp, cnt)          # the stack is sized for depth >= 5
+    with pytest.raises(nq.NQError) as e:
+        nq.sync()
+    assert e.value.code == nq.NQ_ESTACK
+
+
+def test_misaligned_pointer_rejected():
+    pre = nq.enumerate_prefixes(10, 3)
+    raw = torch.zeros(len(pre) * 4 + 1, dtype=torch.int32, device="cuda")
+    mis = raw[1:].view(-1, 4)
+    cnt = torch.zeros(len(pre), dtype=torch.int64, device="cuda")
+    with pytest.raises(nq.NQError) as e:
+        nq.count(10, 3, mis, cnt)
+    assert e.value.code == nq.NQ_EINVAL
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_constrained_against_oracle(orc, seed):
+    g = synth_inputs.SplitMix64(300 + seed)
+    for _ in range(10):
+        n = 4 + g.below(11)        # 4..14
+        qs = synth_inputs.constraint_set(g, n, g.below(5))
+        assert nq.count_constrained(n, qs) == orc.count_constrained(n, qs)[0], (n, qs)
+
+
+def test_constrained_special_cases(orc):
+    for n in range(1, 13):
+        assert nq.count_constrained(n, []) == Q[n]
+    assert nq.count_constrained(8, [(0, 0), (1, 1)]) == 0
+    assert nq.count_constrained(8, [(0, 0), (0, 3)]) == 0
+    assert nq.count_constrained(8, [(3, 3), (3, 3)]) == orc.count_constrained(8, [(3, 3)])[0]
+    assert nq.count_constrained(9, [(8, 4)]) == orc.count_constrained(9, [(8, 4)])[0]
+    assert nq.count_constrained(16, [(15, 2), (0, 7)]) == orc.count_constrained(16, [(15, 2), (0, 7)])[0]
+    with pytest.raises(nq.NQError):
+        nq.count_constrained(8, [(8, 1)])
+
+
+@pytest.mark.slow
+def test_total_n21_n22():
+    assert nq.total(21) == Q[21]
+    assert nq.total(22) == Q[22]
