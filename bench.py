@@ -48,10 +48,11 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=18)
     ap.add_argument("--d", type=int, default=0, help="prefix depth (0 = library default)")
-    ap.add_argument("--layout", default="default", choices=["default", "paper", "reg"])
+    ap.add_argument("--layout", default="default", choices=["default", "paper", "reg", "wt", "wt32", "wt32a", "wtm",
+                                                      "regm"])
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--bps", type=int, default=0, help="blocks per SM (0 = max)")
-    ap.add_argument("--order", type=int, default=0)
+    ap.add_argument("--order", type=int, default=0, help="0 default, 1 index order, 2 reverse")
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -289,20 +290,23 @@ def main():
     ms_per_step = 1e3 * kern_s_max / args.steps
 
     # end to end through the public C call (enumerate, H2D, search, D2H)
-    e2e_times = []
-    e2e_cfg = nq.make_config(args.layout, args.block, args.bps, args.order, d)
-    for k in range(args.e2e_steps + 1):
-        t0 = time.perf_counter()
-        r = nq.total_ex(n, e2e_cfg)
-        dt = time.perf_counter() - t0
-        if r["total"] != total_q:
-            raise SystemExit("end-to-end total differs")
-        if k:  # first call warms the pinned staging buffer
-            e2e_times.append(dt)
-    e2e_s = max_over_ranks(dist, float(np.mean(e2e_times)), device)
-    e2e = {"value": nodes_per_step * world / e2e_s, "unit": UNIT,
-           "h2d_bytes_per_step": m * 16, "d2h_bytes_per_step": 8,
-           "solve_ms": 1e3 * e2e_s, "enumerate_ms": r["enumerate_ms"], "upload_ms": r["upload_ms"]}
+    e2e = None
+    if args.e2e_steps > 0:
+        e2e_times = []
+        e2e_cfg = nq.make_config(args.layout, args.block, args.bps, args.order, d)
+        for k in range(args.e2e_steps + 1):
+            t0 = time.perf_counter()
+            r = nq.total_ex(n, e2e_cfg)
+            dt = time.perf_counter() - t0
+            if r["total"] != total_q:
+                raise SystemExit("end-to-end total differs")
+            if k:  # the first call warms the pinned staging buffer
+                e2e_times.append(dt)
+        e2e_s = max_over_ranks(dist, float(np.mean(e2e_times)), device)
+        e2e = {"value": nodes_per_step * world / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": m * 16, "d2h_bytes_per_step": 8,
+               "solve_ms": 1e3 * e2e_s, "enumerate_ms": r["enumerate_ms"],
+               "upload_ms": r["upload_ms"]}
 
     # roofline of the one kernel: algorithmic int ops per launch / launch time
     props = torch.cuda.get_device_properties(device)

@@ -86,6 +86,17 @@ typedef struct nq_queen {
                              re-read from shared memory every step */
 #define NQ_LAYOUT_REG 2   /* 16-byte frames, the top frame kept in registers; a frame
                              is saved only while it still has untried columns */
+#define NQ_LAYOUT_WT 3    /* 16-byte frames, the top frame in registers and mirrored in
+                             its slot (write-through): the child is built in place and
+                             the frame is restored by one 16-byte load */
+#define NQ_LAYOUT_WT32 4  /* write-through with the frame split into four 32-bit
+                             arrays (cols, ld, rd, avail), each interleaved by thread:
+                             every access is one word in the lane's own bank */
+#define NQ_LAYOUT_WT32A 5 /* WT32 with the disjoint-bit ORs written as additions
+                             (issuable on the FMA pipe as well as the ALU pipe) */
+#define NQ_LAYOUT_WTM 6   /* WT with the step's disjoint-bit arithmetic written as
+                             integer multiply-adds, balancing the FMA and ALU pipes */
+#define NQ_LAYOUT_REGM 7  /* REG with the same multiply-add arithmetic */
 
 /* Launch configuration. Zero in any field selects the library default. */
 typedef struct nq_config {
@@ -93,7 +104,9 @@ typedef struct nq_config {
     int32_t block;         /* threads per block, a multiple of 32, <= 1024 */
     int32_t blocks_per_sm; /* resident blocks per SM (grid = SMs x this); capped at
                               what fits */
-    int32_t order;         /* 0: prefixes claimed in index order; 1: last index first */
+    int32_t order;         /* claim order: 0 default (last index first: canonical order
+                              puts the heavier subtrees late, so they start first),
+                              1 index order, 2 last index first */
     int32_t d;             /* nq_total_ex only: prefix depth 1..N (0 = default) */
     int32_t reserved[3];
 } nq_config;

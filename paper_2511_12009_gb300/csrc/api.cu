@@ -94,8 +94,13 @@ int enqueue_search(const nq_prefix *d_prefixes, uint64_t n, int expect_n, int mi
         a.expect_n = expect_n;
         a.min_d = min_d;
         a.slots = p.slots;
-        a.order = cfg ? cfg->order : 0;
+        // claim order: last index first unless index order is asked for
+        a.order = (cfg && cfg->order == 1) ? 0 : 1;
         if (allowed) std::memcpy(a.allowed, allowed, sizeof(a.allowed));
+        a.mul[0] = 1u;
+        a.mul[1] = 2u;
+        a.mul[2] = 0xFFFFFFFFu;
+        a.mul[3] = 0x80000000u;
         rc = launch_search(a, p, diag, constrained, s);
     }
     cudaFreeAsync(cursor, s);

@@ -23,6 +23,10 @@ struct SearchArgs {
     // Constrained mode only (partial-board queries): the columns each row may
     // take; rows >= N and entry 31 must be 0.
     uint32_t allowed[32];
+    // Multipliers 1, 2, 2^32-1 and 2^31 for the multiply-add form of the step
+    // (layout WTM). Passed at run time so that the compiler cannot fold them:
+    // the products must be issued as integer multiply-adds on the FMA pipe.
+    uint32_t mul[4];
 };
 
 // Constrained mode packs the row index of a frame into bits 27..31 of cols.

@@ -28,6 +28,13 @@ __device__ __forceinline__ void op(uint32_t &a, uint32_t b, uint32_t c) {
     }
 }
 
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// cycles[0] += SM clocks, cycles[1] += nanoseconds, per block, over the same region.
 template <int KIND>
 __global__ void alu_probe(uint32_t *out, unsigned long long *cycles, int iters, uint32_t seed) {
     uint32_t a0 = threadIdx.x ^ seed, a1 = a0 + 1, a2 = a0 + 2, a3 = a0 + 3;
@@ -35,6 +42,7 @@ __global__ void alu_probe(uint32_t *out, unsigned long long *cycles, int iters, 
     const uint32_t b = seed * 3u + 1u, c = seed * 5u + 7u;
     __syncthreads();
     const long long t0 = clock64();
+    const unsigned long long g0 = global_ns();
     for (int i = 0; i < iters; ++i) {
 #pragma unroll
         for (int u = 0; u < 16; ++u) {
@@ -44,8 +52,12 @@ __global__ void alu_probe(uint32_t *out, unsigned long long *cycles, int iters, 
     }
     __syncthreads();
     const long long t1 = clock64();
+    const unsigned long long g1 = global_ns();
     out[blockIdx.x * blockDim.x + threadIdx.x] = a0 ^ a1 ^ a2 ^ a3 ^ a4 ^ a5 ^ a6 ^ a7;
-    if (threadIdx.x == 0) atomicAdd(cycles, (unsigned long long)(t1 - t0));
+    if (threadIdx.x == 0) {
+        atomicAdd(&cycles[0], (unsigned long long)(t1 - t0));
+        atomicAdd(&cycles[1], g1 - g0);
+    }
 }
 
 template <int KIND>
@@ -78,7 +90,7 @@ extern "C" int nq_probe_alu(int kind, int iters, double *per_clk_per_sm, double 
     uint32_t *out = nullptr;
     unsigned long long *cyc = nullptr;
     if (cudaMalloc(&out, (size_t)grid * block * 4) != cudaSuccess) return NQ_ENOMEM;
-    if (cudaMalloc(&cyc, 8) != cudaSuccess) {
+    if (cudaMalloc(&cyc, 16) != cudaSuccess) {
         cudaFree(out);
         return NQ_ENOMEM;
     }
@@ -87,25 +99,26 @@ extern "C" int nq_probe_alu(int kind, int iters, double *per_clk_per_sm, double 
     cudaEventCreate(&e1);
     int rc = NQ_OK;
     float ms = 0;
-    unsigned long long cycles = 0;
+    unsigned long long cycles[2] = {0, 0};
     for (int rep = 0; rep < 2 && rc == NQ_OK; ++rep) {  // the first pass warms up
         uint32_t seed = 12345u + rep;
         void *params[] = {&out, &cyc, &iters, &seed};
-        cudaMemset(cyc, 0, 8);
+        cudaMemset(cyc, 0, 16);
         cudaEventRecord(e0);
         if (cudaLaunchKernel(k, dim3(grid), dim3(block), params, 0, nullptr) != cudaSuccess)
             rc = NQ_ECUDA;
         cudaEventRecord(e1);
         if (cudaEventSynchronize(e1) != cudaSuccess) rc = NQ_ECUDA;
         cudaEventElapsedTime(&ms, e0, e1);
-        cudaMemcpy(&cycles, cyc, 8, cudaMemcpyDeviceToHost);
+        cudaMemcpy(cycles, cyc, 16, cudaMemcpyDeviceToHost);
     }
     const double per_thread = (double)iters * 16.0 * 8.0 * (kind == 4 ? 4.0 : 1.0);
     const double total = per_thread * grid * block;
-    const double mean_cycles = (double)cycles / grid;  // per block
+    // SM clock over the blocks' own intervals; the whole run spans ms at that clock
+    const double mhz = cycles[1] ? (double)cycles[0] / (double)cycles[1] * 1e3 : 0.0;
     *per_s = total / (ms * 1e-3);
-    *per_clk_per_sm = total / (mean_cycles * sms);
-    *sm_mhz = mean_cycles / (ms * 1e3);
+    *per_clk_per_sm = mhz > 0 ? *per_s / (sms * mhz * 1e6) : 0.0;
+    *sm_mhz = mhz;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(out);

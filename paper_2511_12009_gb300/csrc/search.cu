@@ -43,8 +43,8 @@ __device__ int g_status;  // first error any launch recorded on this device
 namespace {
 
 constexpr uint64_t kNone = ~0ull;
-constexpr int kChunk = 16;
-static_assert(kChunk < 32, "the sentinel frame holds 32 idle steps");
+constexpr int kChunk = 15;
+static_assert(kChunk < 16, "the sentinel frame holds 16 idle steps (32 for ~0 masks)");
 constexpr uint32_t kRowInc = 1u << kRowShift;
 // Constrained-mode sentinel: row field 30, so the child is row 31 whose allowed
 // mask is 0 -- no push, no count; its candidate bits stay below the row field,
@@ -57,57 +57,83 @@ extern __shared__ __align__(16) unsigned char nq_smem[];
 
 __device__ __forceinline__ void record_error(int code) { atomicCAS(&g_status, 0, code); }
 
-__device__ __forceinline__ uint4 lds4(uint32_t off) {
-    return *reinterpret_cast<const uint4 *>(nq_smem + off);
+// Shared-memory accesses by 32-bit shared-window address (the kernel keeps
+// every stack position as such an address, based at the dynamic array).
+__device__ __forceinline__ uint4 lds4(uint32_t a) {
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "r"(a)
+                 : "memory");
+    return v;
 }
-__device__ __forceinline__ uint32_t lds1(uint32_t off) {
-    return *reinterpret_cast<const uint32_t *>(nq_smem + off);
+__device__ __forceinline__ uint32_t lds1(uint32_t a) {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    return v;
 }
-__device__ __forceinline__ void sts4(uint32_t off, uint4 v) {
-    *reinterpret_cast<uint4 *>(nq_smem + off) = v;
+__device__ __forceinline__ void sts4(uint32_t a, uint4 v) {
+    asm volatile("st.shared.v4.u32 [%0], {%1, %2, %3, %4};"
+                 :
+                 : "r"(a), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+                 : "memory");
 }
-__device__ __forceinline__ void sts1(uint32_t off, uint32_t v) {
-    *reinterpret_cast<uint32_t *>(nq_smem + off) = v;
+__device__ __forceinline__ void sts1(uint32_t a, uint32_t v) {
+    asm volatile("st.shared.u32 [%0], %1;" : : "r"(a), "r"(v) : "memory");
 }
 
 // True when the child state c2 has exactly one free column left (bits >= N
 // are pre-set), i.e. queens now sit in rows 0..N-2: Algorithm 3's
-// popc(cur) == N-1 test.
-__device__ __forceinline__ bool one_free(uint32_t c2) { return (c2 | (c2 + 1u)) == ~0u; }
+// popc(cur) == N-1 test, which with the pre-set high bits reads popc == 31.
+// The population count runs on a pipe the rest of the step does not use.
+__device__ __forceinline__ bool one_free(uint32_t c2) { return __popc(c2) == 31; }
 
 // Per-lane constants of a step.
 struct Lane {
     uint32_t stride;   // bytes between a thread's consecutive frames
-    uint32_t base;     // byte offset of this thread's slot 0 (the sentinel)
+    uint32_t base;     // shared address of this thread's slot 0 (the sentinel)
     uint32_t limit;    // one past this thread's last slot
-    uint32_t table;    // constrained mode: byte offset of allowed[]
+    uint32_t table;    // WT32: bytes per array; constrained mode: address of allowed[]
     uint32_t thr;      // constrained mode: (N-1) << 27, the last-row threshold
 };
 
 // One step, layout REG: the top frame (c, l, r, av) lives in registers, the
 // stack holds only ancestors that still have untried columns.
-template <bool DIAG, bool CONSTR>
+//
+// MADD (layout REGM): the disjoint-bit arithmetic as integer multiply-adds by
+// run-time multipliers, as in step_wtm, so it issues on the FMA pipe.
+template <bool DIAG, bool CONSTR, bool MADD = false>
 __device__ __forceinline__ void step_reg(uint32_t &c, uint32_t &l, uint32_t &r, uint32_t &av,
                                          uint32_t &top, const Lane &k, uint32_t &s32,
-                                         uint32_t &n32) {
-    const uint32_t p = av & (0u - av);  // lowest free column (Algorithm 2, line 10)
-    const uint32_t ar = av ^ p;         // the columns still to try here
+                                         uint32_t &n32, const uint32_t m1 = 1u,
+                                         const uint32_t m2 = 2u, const uint32_t mneg = ~0u,
+                                         const uint32_t mhalf = 0x80000000u) {
+    uint32_t p, ar, l2, r2;
+    if (MADD) {
+        p = av & (av * mneg);
+        ar = p * mneg + av;
+        l2 = l * m2 + p * m2;
+        r2 = __umulhi(p * m1 + r, mhalf);
+    } else {
+        p = av & (0u - av);  // lowest free column (Algorithm 2, line 10)
+        ar = av ^ p;         // the columns still to try here
+        l2 = (l | p) << 1;
+        r2 = (r | p) >> 1;
+    }
     uint32_t c2, a2;
     bool lastrow;
-    const uint32_t l2 = (l | p) << 1;
-    const uint32_t r2 = (r | p) >> 1;
     if (CONSTR) {
         c2 = (c | p) + kRowInc;
         a2 = ~(c2 | l2 | r2) & lds1(k.table + ((c2 >> kRowShift) << 2));
         lastrow = c2 >= k.thr;
     } else {
-        c2 = c | p;
+        c2 = MADD ? p * m1 + c : c | p;
         a2 = ~(c2 | l2 | r2);  // free columns of the next row
         lastrow = one_free(c2);
     }
     const bool live = a2 != 0u;
     s32 += (lastrow && live) ? 1u : 0u;  // Algorithm 3: count instead of pushing
-    if (DIAG) n32 += (CONSTR ? (c >> kRowShift) < 30u : c != ~0u) ? 1u : 0u;
+    if (DIAG) n32 += (top != k.base) ? 1u : 0u;  // top == base: idle on the sentinel
     const bool push = !lastrow && live;
     if (push && ar != 0u) {
         if (!DIAG || top < k.limit) {
@@ -124,14 +150,201 @@ __device__ __forceinline__ void step_reg(uint32_t &c, uint32_t &l, uint32_t &r, 
             c = f.x; l = f.y; r = f.z; av = f.w;
         } else {
             record_error(NQ_ESTACK);
-            c = CONSTR ? kSentinelC : ~0u;
-            l = r = ~0u;
-            av = CONSTR ? kSentinelAvC : ~0u;
+            c = CONSTR ? kSentinelC : MADD ? 0xAAAAAAAAu : ~0u;
+            l = r = MADD ? 0xAAAAAAAAu : ~0u;
+            av = CONSTR ? kSentinelAvC : MADD ? 0x55555555u : ~0u;
         }
     } else if (push) {
         c = c2; l = l2; r = r2; av = a2;
     } else {
         av = ar;
+    }
+}
+
+// One step, layout REGM (production build): REG's structure, the multiply-add
+// arithmetic of step_wtm, and the control tail -- count, save, pop, and the
+// state moves -- as one block of hand-written PTX with explicit predicates, so
+// that every lane executes the same straight-line code (no divergent branch
+// around the push / pop cases). p is the chosen column, ar the candidates
+// left here, (c2, l2, r2, a2) the child. Operands: %0..%5 = c, l, r, av, top,
+// s32 (updated); %6..%12 = popc(c2), a2, ar, c2, l2, r2, stride.
+__device__ __forceinline__ void step_regm(uint32_t &c, uint32_t &l, uint32_t &r, uint32_t &av,
+                                          uint32_t &top, const uint32_t stride, uint32_t &s32,
+                                          const uint32_t m1, const uint32_t m2,
+                                          const uint32_t mneg, const uint32_t mhalf) {
+    const uint32_t p = av & (av * mneg);
+    const uint32_t ar = p * mneg + av;
+    const uint32_t c2 = p * m1 + c;
+    const uint32_t l2 = l * m2 + p * m2;
+    const uint32_t r2 = __umulhi(p * m1 + r, mhalf);
+    const uint32_t a2 = ~(c2 | l2 | r2);
+    const uint32_t pc = __popc(c2);
+    asm volatile(
+        "{\n\t"
+        ".reg .pred plast, pcnt, ppush, psave, ppop;\n\t"
+        "setp.eq.u32 plast, %6, 31;\n\t"            // queens in rows 0..N-2 (Algorithm 3)
+        "setp.ne.and.u32 pcnt, %7, 0, plast;\n\t"   // ... and row N-1 has its column free
+        "setp.ne.and.u32 ppush, %7, 0, !plast;\n\t" // a live child above the last row
+        "@pcnt add.u32 %5, %5, 1;\n\t"
+        "setp.ne.and.u32 psave, %8, 0, ppush;\n\t"  // keep this frame: it has columns left
+        "setp.eq.and.u32 ppop, %8, 0, !ppush;\n\t"  // exhausted, nothing pushed: pop
+        "@psave st.shared.v4.u32 [%4], {%0, %1, %2, %8};\n\t"
+        "@psave add.u32 %4, %4, %12;\n\t"
+        "@ppop sub.u32 %4, %4, %12;\n\t"
+        "selp.b32 %3, %7, %8, ppush;\n\t"
+        "@ppush mov.b32 %0, %9;\n\t"
+        "@ppush mov.b32 %1, %10;\n\t"
+        "@ppush mov.b32 %2, %11;\n\t"
+        "@ppop ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];\n\t"
+        "}"
+        : "+r"(c), "+r"(l), "+r"(r), "+r"(av), "+r"(top),
+          "+r"(s32)
+        : "r"(pc), "r"(a2), "r"(ar), "r"(c2), "r"(l2), "r"(r2),
+          "r"(stride)
+        : "memory");
+}
+
+// One step, layout WT (write-through): the top frame lives in registers AND in
+// its stack slot. The child is computed in place; when it is pushed it is
+// written through to the next slot (after the parent's slot gets its
+// remaining candidates), otherwise the registers are reloaded from the slot
+// (the frame itself, or its parent when the frame has no column left). A
+// frame whose last column is taken is replaced by its child, so the stack
+// only ever holds frames with untried columns.
+template <bool DIAG>
+__device__ __forceinline__ void step_wt(uint32_t &c, uint32_t &l, uint32_t &r, uint32_t &av,
+                                        uint32_t &top, const Lane &k, uint32_t &s32,
+                                        uint32_t &n32) {
+    if (DIAG) n32 += (c != ~0u) ? 1u : 0u;
+    const uint32_t p = av & (0u - av);
+    const uint32_t ar = av ^ p;
+    c |= p;
+    l = (l | p) << 1;
+    r = (r | p) >> 1;
+    av = ~(c | l | r);
+    const bool lastrow = one_free(c);
+    const bool live = av != 0u;
+    s32 += (lastrow && live) ? 1u : 0u;
+    if (!lastrow && live) {
+        sts1(top + 12u, ar);
+        const uint32_t nt = top + (ar != 0u ? k.stride : 0u);
+        if (!DIAG || nt < k.limit) {
+            top = nt;
+            sts4(top, make_uint4(c, l, r, av));
+        } else {
+            record_error(NQ_ESTACK);
+        }
+    } else {
+        if (ar == 0u) {
+            if (!DIAG || top > k.base) top -= k.stride;
+            else record_error(NQ_ESTACK);
+        }
+        const uint4 f = lds4(top);
+        c = f.x; l = f.y; r = f.z;
+        av = ar != 0u ? ar : f.w;
+    }
+}
+
+// One step, layout WT32: the write-through scheme of WT with the frame split
+// into four 32-bit arrays (cols, ld, rd, avail), each interleaved by thread,
+// so that every shared-memory access is a 32-bit word in the lane's own bank
+// (the paper's per-int layout, Section 3.1). Only the avail word of a frame
+// is ever updated in place, and a child's initial avail is never stored: a
+// frame's avail slot is read only after the frame has pushed a child, and the
+// push writes it.
+//
+// ARITH: p is always a column no queen attacks in this row, so cols | p,
+// (ld | p), (rd | p) and avail ^ p equal cols + p, ld + p, rd + p and
+// avail - p. Written as additions they may be issued on the FMA pipe (IMAD)
+// instead of the ALU pipe. The idle sentinel then uses alternating bits so
+// that its column is never in its own masks either.
+template <bool DIAG, bool ARITH>
+__device__ __forceinline__ void step_wt32(uint32_t &c, uint32_t &l, uint32_t &r, uint32_t &av,
+                                          uint32_t &top, const Lane &k, uint32_t &s32,
+                                          uint32_t &n32) {
+    const uint32_t A = k.table;  // bytes per array
+    if (DIAG) n32 += (c != (ARITH ? 0xAAAAAAAAu : ~0u)) ? 1u : 0u;
+    const uint32_t p = av & (0u - av);
+    uint32_t ar;
+    if (ARITH) {
+        ar = av - p;
+        c = c + p;
+        l = (l + p) << 1;
+        r = (r + p) >> 1;
+    } else {
+        ar = av ^ p;
+        c |= p;
+        l = (l | p) << 1;
+        r = (r | p) >> 1;
+    }
+    av = ~(c | l | r);
+    const bool lastrow = one_free(c);
+    const bool live = av != 0u;
+    s32 += (lastrow && live) ? 1u : 0u;
+    if (!lastrow && live) {
+        sts1(top + 3u * A, ar);
+        const uint32_t nt = top + (ar != 0u ? k.stride : 0u);
+        if (!DIAG || nt < k.limit) {
+            top = nt;
+            sts1(top, c);
+            sts1(top + A, l);
+            sts1(top + 2u * A, r);
+        } else {
+            record_error(NQ_ESTACK);
+        }
+    } else {
+        if (ar == 0u) {
+            if (!DIAG || top > k.base) top -= k.stride;
+            else record_error(NQ_ESTACK);
+        }
+        c = lds1(top);
+        l = lds1(top + A);
+        r = lds1(top + 2u * A);
+        av = ar != 0u ? ar : lds1(top + 3u * A);
+    }
+}
+
+// One step, layout WTM: the WT scheme with the arithmetic balanced across
+// two pipes. Because p is a column that no queen attacks in this row, the bit
+// operations of the step are exact additions: cols | p = cols + p,
+// (ld | p) << 1 = 2 ld + 2p, (rd | p) >> 1 = hi32((rd + p) * 2^31),
+// avail ^ p = avail - p, and -avail = avail * (2^32 - 1). Written as
+// multiply-adds by run-time multipliers (m1 = 1, m2 = 2, mneg = 2^32-1,
+// mhalf = 2^31) they run on the FMA pipe, leaving the ALU pipe the two
+// lop3s, the compares and the selects. The idle sentinel uses alternating
+// bits (its column is never in its own masks, so the sums stay exact).
+template <bool DIAG>
+__device__ __forceinline__ void step_wtm(uint32_t &c, uint32_t &l, uint32_t &r, uint32_t &av,
+                                         uint32_t &top, const Lane &k, const uint32_t m1,
+                                         const uint32_t m2, const uint32_t mneg,
+                                         const uint32_t mhalf, uint32_t &s32, uint32_t &n32) {
+    if (DIAG) n32 += (top != k.base) ? 1u : 0u;
+    const uint32_t p = av & (av * mneg);   // lowest free column
+    const uint32_t ar = p * mneg + av;     // avail - p
+    c = p * m1 + c;                        // cols + p
+    l = l * m2 + p * m2;                   // (ld + p) << 1
+    r = __umulhi(p * m1 + r, mhalf);       // (rd + p) >> 1
+    av = ~(c | l | r);
+    const bool lastrow = one_free(c);
+    const bool live = av != 0u;
+    s32 += (lastrow && live) ? 1u : 0u;
+    if (!lastrow && live) {
+        sts1(top + 12u, ar);
+        const uint32_t nt = top + (ar != 0u ? k.stride : 0u);
+        if (!DIAG || nt < k.limit) {
+            top = nt;
+            sts4(top, make_uint4(c, l, r, av));
+        } else {
+            record_error(NQ_ESTACK);
+        }
+    } else {
+        if (ar == 0u) {
+            if (!DIAG || top > k.base) top -= k.stride;
+            else record_error(NQ_ESTACK);
+        }
+        const uint4 f = lds4(top);
+        c = f.x; l = f.y; r = f.z;
+        av = ar != 0u ? ar : f.w;
     }
 }
 
@@ -148,7 +361,10 @@ __device__ __forceinline__ void step_paper(uint32_t &top, const Lane &k, uint32_
     const uint4 f = lds4(top - k.stride);
     const uint32_t p = f.w & (0u - f.w);
     const uint32_t ar = f.w ^ p;
-    sts1(top - k.stride + 12u, ar);
+    // Algorithm 2 writes back only valid_pos; writing the whole 16-byte frame
+    // costs the same four wavefronts and keeps the quarter-warp phases free of
+    // bank conflicts (a 32-bit store at a 16-byte lane stride is 4-way).
+    sts4(top - k.stride, make_uint4(f.x, f.y, f.z, ar));
     if (ar == 0u) top -= k.stride;
     const uint32_t c2 = f.x | p;
     const uint32_t l2 = (f.y | p) << 1;
@@ -170,31 +386,49 @@ __device__ __forceinline__ void step_paper(uint32_t &top, const Lane &k, uint32_
 
 template <int LAYOUT, bool DIAG, bool CONSTR>
 __global__ void __launch_bounds__(1024, 1) search_kernel(const SearchArgs a) {
-    constexpr bool kReg = LAYOUT == NQ_LAYOUT_REG;
+    constexpr bool kRegm = LAYOUT == NQ_LAYOUT_REGM;
+    constexpr bool kReg = LAYOUT == NQ_LAYOUT_REG || kRegm;
+    constexpr bool kWt = LAYOUT == NQ_LAYOUT_WT;
+    constexpr bool kWt32 = LAYOUT == NQ_LAYOUT_WT32 || LAYOUT == NQ_LAYOUT_WT32A;
+    constexpr bool kWtm = LAYOUT == NQ_LAYOUT_WTM;
+    constexpr bool kArith = LAYOUT == NQ_LAYOUT_WT32A || kWtm || kRegm;  // alternating sentinel
+    constexpr bool kRegs = kReg || kWt || kWt32 || kWtm;  // top frame held in registers
     static_assert(kReg || !CONSTR, "constrained mode uses the REG layout");
+    constexpr uint32_t kElem = kWt32 ? 4u : 16u;  // bytes of one slot in one array
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(nq_smem);
     Lane k;
-    k.stride = blockDim.x * 16u;
-    k.base = threadIdx.x * 16u;
+    k.stride = blockDim.x * kElem;
+    k.base = sbase + threadIdx.x * kElem;
     k.limit = k.base + (uint32_t)a.slots * k.stride;
-    k.table = (uint32_t)a.slots * k.stride;
+    // WT32: bytes per array; constrained mode: address of allowed[] after the stacks
+    k.table = kWt32 ? (uint32_t)a.slots * k.stride : sbase + (uint32_t)a.slots * k.stride;
     k.thr = 0;
     const unsigned lane = threadIdx.x & 31u;
     const unsigned lt_mask = (1u << lane) - 1u;
+    const uint32_t m1 = a.mul[0], m2 = a.mul[1], mneg = a.mul[2], mhalf = a.mul[3];
     if (CONSTR) {
         if (threadIdx.x < 32) sts1(k.table + threadIdx.x * 4u, a.allowed[threadIdx.x]);
         __syncthreads();
     }
-    const uint32_t sent_c = CONSTR ? kSentinelC : ~0u;
-    const uint32_t sent_av = CONSTR ? kSentinelAvC : ~0u;
+    const uint32_t sent_c = CONSTR ? kSentinelC : kArith ? 0xAAAAAAAAu : ~0u;
+    const uint32_t sent_lr = kArith ? 0xAAAAAAAAu : ~0u;
+    const uint32_t sent_av = CONSTR ? kSentinelAvC : kArith ? 0x55555555u : ~0u;
 
-    uint32_t c = sent_c, l = ~0u, r = ~0u, av = sent_av;  // REG: the top frame
-    uint32_t top = k.base;                            // byte offset: next free slot
-    // Slot 0 of every stack holds the sentinel frame. REG pops it when a
-    // subproblem is exhausted (the lane then idles on it until the next
-    // bookkeeping point); PAPER keeps it as the top frame while idle.
-    sts4(k.base, make_uint4(sent_c, ~0u, ~0u, sent_av));
-    if (!kReg) top = k.base + k.stride;
-    const uint32_t idle_top = kReg ? k.base : k.base + k.stride;
+    uint32_t c = sent_c, l = sent_lr, r = sent_lr, av = sent_av;  // the top frame
+    uint32_t top = k.base;                                       // byte offset
+    // Slot 0 of every stack holds the sentinel frame. The register layouts pop
+    // it when a subproblem is exhausted (the lane then idles on it until the
+    // next bookkeeping point); PAPER keeps it as the top frame while idle.
+    if (kWt32) {
+        sts1(k.base, sent_c);
+        sts1(k.base + k.table, sent_lr);
+        sts1(k.base + 2u * k.table, sent_lr);
+        sts1(k.base + 3u * k.table, sent_av);
+    } else {
+        sts4(k.base, make_uint4(sent_c, sent_lr, sent_lr, sent_av));
+    }
+    if (!kRegs) top = k.base + k.stride;
+    const uint32_t idle_top = kRegs ? k.base : k.base + k.stride;
 
     uint64_t idx = kNone;   // subproblem in progress
     uint32_t wt = 0, pn = 0;
@@ -224,9 +458,9 @@ __global__ void __launch_bounds__(1024, 1) search_kernel(const SearchArgs a) {
                 finish(idx, sol, nod + sol, wt, pn);
                 idx = kNone;
             }
-            if (kReg) {
+            if (kRegs) {
                 c = sent_c;
-                l = r = ~0u;
+                l = r = sent_lr;
                 av = sent_av;
             } else {
                 sts1(k.base + 12u, ~0u);
@@ -255,6 +489,8 @@ __global__ void __launch_bounds__(1024, 1) search_kernel(const SearchArgs a) {
                                     (uint32_t)__popc(P.x) == d &&
                                     (!CONSTR || n <= (uint32_t)kMaxConstrainedN);
                     const int need_slots = kReg ? (int)n - 1 - (int)d : (int)n - (int)d;
+                    // (REG: sentinel + ancestors of rows d..N-3; WT / PAPER: sentinel +
+                    // frames of rows d..N-2)
                     if (!ok) {
                         record_error(NQ_EINVAL);
                         finish(pi, 0, 0, 0, 0);
@@ -283,6 +519,16 @@ __global__ void __launch_bounds__(1024, 1) search_kernel(const SearchArgs a) {
                             if (kReg) {
                                 c = c0; l = l0; r = r0; av = a0;
                                 top = k.base + k.stride;  // above the sentinel
+                            } else if (kWt || kWtm) {
+                                c = c0; l = l0; r = r0; av = a0;
+                                top = k.base + k.stride;  // the frame's own slot
+                                sts4(top, make_uint4(c0, l0, r0, a0));
+                            } else if (kWt32) {
+                                c = c0; l = l0; r = r0; av = a0;
+                                top = k.base + k.stride;
+                                sts1(top, c0);
+                                sts1(top + k.table, l0);
+                                sts1(top + 2u * k.table, r0);
                             } else {
                                 sts4(k.base + k.stride, make_uint4(c0, l0, r0, a0));
                                 top = k.base + 2u * k.stride;
@@ -299,8 +545,18 @@ __global__ void __launch_bounds__(1024, 1) search_kernel(const SearchArgs a) {
         uint32_t s32 = 0, n32 = 0;
 #pragma unroll
         for (int j = 0; j < kChunk; ++j) {
-            if (kReg)
+            if (kRegm && DIAG)
+                step_reg<DIAG, false, true>(c, l, r, av, top, k, s32, n32, m1, m2, mneg, mhalf);
+            else if (kRegm)
+                step_regm(c, l, r, av, top, k.stride, s32, m1, m2, mneg, mhalf);
+            else if (kReg)
                 step_reg<DIAG, CONSTR>(c, l, r, av, top, k, s32, n32);
+            else if (kWt)
+                step_wt<DIAG>(c, l, r, av, top, k, s32, n32);
+            else if (kWt32)
+                step_wt32<DIAG, kArith>(c, l, r, av, top, k, s32, n32);
+            else if (kWtm)
+                step_wtm<DIAG>(c, l, r, av, top, k, m1, m2, mneg, mhalf, s32, n32);
             else
                 step_paper<DIAG>(top, k, s32, n32);
         }
@@ -338,6 +594,21 @@ void *pick_kernel(int layout, bool diag, bool constrained) {
     if (layout == NQ_LAYOUT_PAPER)
         return diag ? kernel_ptr<NQ_LAYOUT_PAPER, true, false>()
                     : kernel_ptr<NQ_LAYOUT_PAPER, false, false>();
+    if (layout == NQ_LAYOUT_WT)
+        return diag ? kernel_ptr<NQ_LAYOUT_WT, true, false>()
+                    : kernel_ptr<NQ_LAYOUT_WT, false, false>();
+    if (layout == NQ_LAYOUT_WT32)
+        return diag ? kernel_ptr<NQ_LAYOUT_WT32, true, false>()
+                    : kernel_ptr<NQ_LAYOUT_WT32, false, false>();
+    if (layout == NQ_LAYOUT_WT32A)
+        return diag ? kernel_ptr<NQ_LAYOUT_WT32A, true, false>()
+                    : kernel_ptr<NQ_LAYOUT_WT32A, false, false>();
+    if (layout == NQ_LAYOUT_WTM)
+        return diag ? kernel_ptr<NQ_LAYOUT_WTM, true, false>()
+                    : kernel_ptr<NQ_LAYOUT_WTM, false, false>();
+    if (layout == NQ_LAYOUT_REGM)
+        return diag ? kernel_ptr<NQ_LAYOUT_REGM, true, false>()
+                    : kernel_ptr<NQ_LAYOUT_REGM, false, false>();
     return diag ? kernel_ptr<NQ_LAYOUT_REG, true, false>()
                 : kernel_ptr<NQ_LAYOUT_REG, false, false>();
 }
@@ -345,7 +616,8 @@ void *pick_kernel(int layout, bool diag, bool constrained) {
 }  // namespace
 
 int slots_needed(int layout, int max_n, int min_d) {
-    int s = (layout == NQ_LAYOUT_PAPER) ? max_n - min_d : max_n - 1 - min_d;
+    const bool reg = layout == NQ_LAYOUT_REG || layout == NQ_LAYOUT_REGM;
+    int s = reg ? max_n - 1 - min_d : max_n - min_d;
     return s < 1 ? 1 : s;
 }
 
@@ -360,8 +632,8 @@ int make_plan(int max_n, int min_d, bool diag, bool constrained, const nq_config
             cudaSuccess)
         return NQ_ECUDA;
     Plan p{};
-    p.layout = (cfg && cfg->layout) ? cfg->layout : NQ_LAYOUT_REG;
-    if (p.layout != NQ_LAYOUT_PAPER && p.layout != NQ_LAYOUT_REG) return NQ_EINVAL;
+    p.layout = (cfg && cfg->layout) ? cfg->layout : NQ_LAYOUT_REGM;
+    if (p.layout < NQ_LAYOUT_PAPER || p.layout > NQ_LAYOUT_REGM) return NQ_EINVAL;
     if (constrained) p.layout = NQ_LAYOUT_REG;
     p.block = (cfg && cfg->block) ? cfg->block : 256;
     if (p.block < 32 || p.block > 1024 || p.block % 32) return NQ_EINVAL;

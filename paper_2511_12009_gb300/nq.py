@@ -18,8 +18,10 @@ from . import _build
 
 NQ_OK, NQ_EINVAL, NQ_ENOMEM, NQ_ECUDA, NQ_EOVERFLOW, NQ_ETIMEOUT, NQ_ESTACK, NQ_EBUSY = (
     0, -1, -2, -3, -4, -5, -6, -7)
-NQ_LAYOUT_DEFAULT, NQ_LAYOUT_PAPER, NQ_LAYOUT_REG = 0, 1, 2
-LAYOUTS = {"default": 0, "paper": 1, "reg": 2}
+NQ_LAYOUT_DEFAULT, NQ_LAYOUT_PAPER, NQ_LAYOUT_REG, NQ_LAYOUT_WT = 0, 1, 2, 3
+NQ_LAYOUT_WT32, NQ_LAYOUT_WT32A, NQ_LAYOUT_WTM, NQ_LAYOUT_REGM = 4, 5, 6, 7
+LAYOUTS = {"default": 0, "paper": 1, "reg": 2, "wt": 3, "wt32": 4, "wt32a": 5, "wtm": 6,
+           "regm": 7}
 NQ_MAX_N = 31
 
 # numpy view of nq_prefix {u32 cols, ld, rd, meta}

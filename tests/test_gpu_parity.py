@@ -20,7 +20,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 Q = {int(k): v for k, v in json.load(open(os.path.join(GOLDEN, "oeis_a000170.json")))["Q"].items()}
-LAYOUTS = ["paper", "reg"]
+LAYOUTS = ["paper", "reg", "wt", "wt32", "wt32a", "wtm", "regm"]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -28,6 +28,16 @@ def _cuda():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     nq.lib()
+
+
+_ORACLE = {}
+
+
+def oracle_counts(orc, n, d):
+    """Per-prefix (counts, nodes) of the canonical depth-d set, cached per (N, d)."""
+    if (n, d) not in _ORACLE:
+        _ORACLE[(n, d)] = orc.count_prefixes(n, orc.prefixes(n, d)[0])
+    return _ORACLE[(n, d)]
 
 
 def u64(t):
@@ -55,8 +65,7 @@ def weighted(pre, counts):
                                  (14, 3), (14, 6), (15, 5), (16, 5)])
 def test_per_prefix_counts_and_nodes(orc, layout, n, d):
     pre = nq.enumerate_prefixes(n, d)
-    cols, _ = orc.prefixes(n, d)
-    want_c, want_n = orc.count_prefixes(n, cols)
+    want_c, want_n = oracle_counts(orc, n, d)
     got_c, got_n, tot = run(pre, d, n, layout, nodes=True)
     assert np.array_equal(got_c, want_c)
     assert np.array_equal(got_n, want_n)
@@ -91,8 +100,8 @@ def test_launch_shapes(orc, layout):
     """Block sizes, blocks per SM and claim order do not change any count."""
     n, d = 13, 4
     pre = nq.enumerate_prefixes(n, d)
-    want, _ = orc.count_prefixes(n, orc.prefixes(n, d)[0])
-    for block, bps, order in [(32, 1, 0), (64, 3, 1), (128, 0, 0), (512, 1, 1), (1024, 0, 0)]:
+    want, _ = oracle_counts(orc, n, d)
+    for block, bps, order in [(32, 1, 0), (64, 3, 1), (128, 0, 2), (512, 1, 1), (1024, 0, 0)]:
         got, _, tot = run(pre, d, n, layout, block=block, blocks_per_sm=bps, order=order)
         assert np.array_equal(got, want), (block, bps, order)
         assert int(tot[n]) == Q[n]
@@ -134,14 +143,15 @@ def test_empty_batch():
     assert len(got) == 0 and int(tot.sum()) == 0
 
 
-def test_degenerate_prefixes(orc):
+@pytest.mark.parametrize("layout", LAYOUTS)
+def test_degenerate_prefixes(orc, layout):
     """d = N (the prefixes are solutions), d = N - 1 (one row left), and
     prefixes whose next row is already dead."""
     for n in (6, 8, 9):
         for d in (n, n - 1, n - 2):
             pre = nq.enumerate_prefixes(n, d)
-            want, want_n = orc.count_prefixes(n, orc.prefixes(n, d)[0])
-            got, got_n, tot = run(pre, d, n, nodes=True)
+            want, want_n = oracle_counts(orc, n, d)
+            got, got_n, tot = run(pre, d, n, layout, nodes=True)
             assert np.array_equal(got, want) and np.array_equal(got_n, want_n)
             assert int(tot[n]) == Q[n]
 
