@@ -158,12 +158,9 @@ def oracle_rate(n: int, d: int, seconds: float, seed: int = 7) -> dict:
     """The CPU oracle (all host cores, dynamic pulling) on a seeded sample of the
     same workload's subproblems, grown until it has run about `seconds`."""
     import oracle
-    import synth_inputs
     oracle.build()
     cols, _ = oracle.prefixes(n, d)
-    order = synth_inputs.sample_indices(seed, len(cols), min(len(cols), 200000))
-    rng_order = np.array(order, dtype=np.int64)
-    np.random.default_rng(seed).shuffle(rng_order)
+    rng_order = np.random.default_rng(seed).permutation(len(cols))  # seeded, no repeats
     done_nodes, done = 0, 0
     chunk = 64
     t0 = time.perf_counter()
