@@ -221,6 +221,32 @@ int nq_total_ex(int N, const nq_config *cfg, uint64_t *total_out, uint64_t *node
  */
 int nq_count_constrained(int N, const nq_queen *q, int k, uint64_t *count_out);
 
+/*
+ * Counting with no memory allocation at all (the paper has no counterpart;
+ * this is a deployment aid). Some callers cannot let a library allocate: a
+ * serving process that reserved its whole device-memory budget at start-up
+ * (a cudaMalloc in mid-run could fail with out-of-memory, synchronises the
+ * device and stalls the request path), or a program whose framework's
+ * caching allocator owns the GPU's memory. This form of nq_count takes HOST
+ * arrays -- h_prefixes[n] in, h_counts[n] out (raw solutions per prefix),
+ * total_out optional (sum of weight x count) -- and keeps the device side in
+ * one fixed static array inside libnq, sized for NQ_NOALLOC_MAX_PREFIXES
+ * records (about 6.3 MB, held on every GPU that loads libnq until the
+ * process exits). It calls no cudaMalloc, cudaFree or other allocating
+ * routine, and creates no stream or event: it works on `stream`
+ * (synchronously: results are on the host when it returns).
+ *   - n > NQ_NOALLOC_MAX_PREFIXES: returns NQ_EOVERFLOW, nothing is done.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - Every call reuses the same array and zeroes what must start at zero.
+ *     Two calls whose GPU work overlapped would race on it, so each call
+ *     holds a process-wide lock until its results are back on the host.
+ * Record checks and status codes are those of nq_count.
+ */
+#define NQ_NOALLOC_MAX_PREFIXES (1u << 18)
+int nq_count_host_noalloc(int N, int d, const nq_prefix *h_prefixes, uint64_t n,
+                          uint64_t *h_counts, uint64_t *total_out, void *stream);
+
 /* ------------------------------------------------------------------------- */
 /* Measurement (not in the paper): the integer roofline's denominator.        */
 /* ------------------------------------------------------------------------- */
