@@ -108,7 +108,8 @@ typedef struct nq_config {
                               puts the heavier subtrees late, so they start first),
                               1 index order, 2 last index first */
     int32_t d;             /* nq_total_ex only: prefix depth 1..N (0 = default) */
-    int32_t reserved[3];
+    int32_t claim;         /* subproblems a lane claims per atomic (work chunk), 1..64 */
+    int32_t reserved[2];
 } nq_config;
 
 /* Timing of one nq_total_ex call, host wall clock in milliseconds. */
@@ -220,6 +221,48 @@ int nq_total_ex(int N, const nq_config *cfg, uint64_t *total_out, uint64_t *node
  * attack each other (or share a row) give 0. Synchronous.
  */
 int nq_count_constrained(int N, const nq_queen *q, int k, uint64_t *count_out);
+
+/* ------------------------------------------------------------------------- */
+/* Batched counting: several board sizes in one persistent launch replayed   */
+/* from a CUDA graph (the decomposition of Section 1 applied to each board;  */
+/* batching itself is not in the paper).                                      */
+/* ------------------------------------------------------------------------- */
+
+typedef struct nq_batch nq_batch;
+
+/*
+ * Enumerate the symmetric prefix sets of boards ns[0..k-1] (distinct, 1..28;
+ * ds[i] = depth, 0 or ds == NULL for the default), upload their union once
+ * (records by increasing N, claimed heaviest-first), and capture a CUDA graph:
+ * zero the work cursor and per-N totals, one search launch over the union,
+ * copy the totals to pinned host memory. cfg (may be NULL) as in nq_count_ex.
+ * The batch owns its device and pinned buffers until nq_batch_destroy.
+ */
+int nq_batch_create(const int *ns, const int *ds, int k, const nq_config *cfg, nq_batch **out);
+
+/* Records in the union, smallest depth, largest N, launch grid and block. */
+int nq_batch_info(const nq_batch *b, uint64_t *records, int *min_d, int *max_n, int *grid,
+                  int *block);
+
+/*
+ * Replay the graph on `stream` and wait. totals_out[i] = Q(ns[i]) (caller's
+ * order); ms_out = CUDA-event time of the replay. Synchronous.
+ */
+int nq_batch_run(nq_batch *b, void *stream, uint64_t *totals_out, float *ms_out);
+
+/*
+ * The same work as one plain launch per board (each with its own stack size
+ * and occupancy), back to back on `stream`: the baseline the graph is
+ * compared with. Same outputs as nq_batch_run.
+ */
+int nq_batch_run_separate(nq_batch *b, void *stream, uint64_t *totals_out, float *ms_out);
+
+/* Per-prefix solution counts of board `board` (index into ns) from the last run,
+ * in the canonical order of that board's prefix set; size query with h_counts NULL. */
+int nq_batch_counts(const nq_batch *b, int board, uint64_t *h_counts, uint64_t cap,
+                    uint64_t *n_out);
+
+void nq_batch_destroy(nq_batch *b);
 
 /*
  * Counting with no memory allocation at all (the paper has no counterpart;

@@ -183,3 +183,30 @@ def total_sym(n: int, d: int, threads: int | None = None) -> tuple[int, int]:
     counts, nodes = count_prefixes(n, cols, threads)
     return (int(sum(int(a) * int(b) for a, b in zip(w, counts))),
             int(sum(int(x) for x in nodes)))
+
+
+def descendants(n: int, cols_list, rows: int) -> list[tuple[int, ...]]:
+    """All placements extending the queens cols_list (row r in column cols_list[r])
+    by `rows` more rows, in canonical order (rows top-down, columns increasing),
+    as column tuples. Plain Python: no symmetry rule applies below row 1."""
+    base = [int(c) for c in cols_list]
+    d = len(base)
+    out: list[tuple[int, ...]] = []
+
+    def free(placed, r, c):
+        for rr, cc in enumerate(placed):
+            if cc == c or abs(cc - c) == r - rr:
+                return False
+        return True
+
+    def rec(placed):
+        if len(placed) == d + rows:
+            out.append(tuple(placed))
+            return
+        r = len(placed)
+        for c in range(n):
+            if free(placed, r, c):
+                rec(placed + [c])
+
+    rec(base)
+    return out

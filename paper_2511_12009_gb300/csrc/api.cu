@@ -96,6 +96,7 @@ int enqueue_search(const nq_prefix *d_prefixes, uint64_t n, int expect_n, int mi
         a.slots = p.slots;
         // claim order: last index first unless index order is asked for
         a.order = (cfg && cfg->order == 1) ? 0 : 1;
+        a.claim = (cfg && cfg->claim > 0) ? cfg->claim : 1;
         if (allowed) std::memcpy(a.allowed, allowed, sizeof(a.allowed));
         a.mul[0] = 1u;
         a.mul[1] = 2u;

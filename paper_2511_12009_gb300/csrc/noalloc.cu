@@ -81,6 +81,7 @@ extern "C" int nq_count_host_noalloc(int N, int d, const nq_prefix *h_prefixes, 
     a.min_d = d;
     a.slots = plan.slots;
     a.order = 1;
+    a.claim = 1;
     a.mul[0] = 1u;
     a.mul[1] = 2u;
     a.mul[2] = 0xFFFFFFFFu;

@@ -20,6 +20,7 @@ struct SearchArgs {
     int min_d;                     // records with fewer rows placed are rejected (NQ_ESTACK)
     int slots;                     // stack slots (16-byte frames) per thread
     int order;                     // 1: claim the last index first
+    int claim;                     // consecutive indices a lane claims at once (>= 1)
     // Constrained mode only (partial-board queries): the columns each row may
     // take; rows >= N and entry 31 must be 0.
     uint32_t allowed[32];

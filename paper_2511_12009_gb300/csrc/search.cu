@@ -385,7 +385,7 @@ __device__ __forceinline__ void step_paper(uint32_t &top, const Lane &k, uint32_
 }
 
 template <int LAYOUT, bool DIAG, bool CONSTR>
-__global__ void __launch_bounds__(1024, 1) search_kernel(const SearchArgs a) {
+__global__ void __maxnreg__(48) search_kernel(const SearchArgs a) {
     constexpr bool kRegm = LAYOUT == NQ_LAYOUT_REGM;
     constexpr bool kReg = LAYOUT == NQ_LAYOUT_REG || kRegm;
     constexpr bool kWt = LAYOUT == NQ_LAYOUT_WT;
@@ -436,6 +436,8 @@ __global__ void __launch_bounds__(1024, 1) search_kernel(const SearchArgs a) {
     uint64_t wsum = 0;      // weighted solutions not yet in totals[wsum_n]
     uint32_t wsum_n = 0;
     bool exhausted = false;
+    uint64_t next_i = 0;  // claimed, not yet started: next_i .. next_i + rem - 1
+    uint32_t rem = 0;
 
     auto finish = [&](uint64_t i, uint64_t s, uint64_t nodes_below, uint32_t w, uint32_t n) {
         if (a.counts) a.counts[i] = s;
@@ -469,17 +471,32 @@ __global__ void __launch_bounds__(1024, 1) search_kernel(const SearchArgs a) {
         bool need = idle && !exhausted;
         unsigned need_mask = __ballot_sync(~0u, need);
         while (need_mask) {
-            const int leader = __ffs(need_mask) - 1;
-            unsigned long long first = 0;
-            if ((int)lane == leader)
-                first = atomicAdd(a.cursor, (unsigned long long)__popc(need_mask));
-            first = __shfl_sync(~0u, first, leader);
+            // Lanes whose claimed range is used up take the next a.claim indices;
+            // one atomicAdd serves the whole warp.
+            const bool want = need && rem == 0u;
+            const unsigned want_mask = __ballot_sync(~0u, want);
+            if (want_mask) {
+                const uint32_t claim = a.claim > 0 ? (uint32_t)a.claim : 1u;
+                const int leader = __ffs(want_mask) - 1;
+                unsigned long long first = 0;
+                if ((int)lane == leader)
+                    first = atomicAdd(a.cursor,
+                                      (unsigned long long)__popc(want_mask) * (unsigned long long)claim);
+                first = __shfl_sync(~0u, first, leader);
+                if (want) {
+                    next_i = first + (uint64_t)__popc(want_mask & lt_mask) * claim;
+                    if (next_i >= a.n) {
+                        exhausted = true;
+                        need = false;
+                    } else {
+                        rem = a.n - next_i < claim ? (uint32_t)(a.n - next_i) : claim;
+                    }
+                }
+            }
             if (need) {
-                const uint64_t my = first + (uint64_t)__popc(need_mask & lt_mask);
-                if (my >= a.n) {
-                    exhausted = true;
-                    need = false;
-                } else {
+                const uint64_t my = next_i++;
+                --rem;
+                {
                     const uint64_t pi = a.order ? a.n - 1 - my : my;
                     const uint4 P = __ldg(reinterpret_cast<const uint4 *>(a.pre) + pi);
                     const uint32_t n = (P.w >> 2) & 31u, d = (P.w >> 7) & 31u, w = P.w & 3u;

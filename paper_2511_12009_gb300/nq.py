@@ -37,7 +37,8 @@ class NQError(RuntimeError):
 class Config(ctypes.Structure):
     _fields_ = [("layout", ctypes.c_int32), ("block", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("order", ctypes.c_int32),
-                ("d", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("d", ctypes.c_int32), ("claim", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class Timing(ctypes.Structure):
@@ -74,6 +75,15 @@ def _declare(lib):
         "nq_strerror": (ctypes.c_char_p, [_i32]),
         "nq_probe_alu": (_i32, [_i32, _i32, ctypes.POINTER(ctypes.c_double),
                                 ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
+        "nq_batch_create": (_i32, [ctypes.POINTER(_i32), ctypes.POINTER(_i32), _i32,
+                                   ctypes.POINTER(Config), ctypes.POINTER(_vp)]),
+        "nq_batch_info": (_i32, [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_i32),
+                                 ctypes.POINTER(_i32), ctypes.POINTER(_i32), ctypes.POINTER(_i32)]),
+        "nq_batch_run": (_i32, [_vp, _vp, ctypes.POINTER(_u64), ctypes.POINTER(ctypes.c_float)]),
+        "nq_batch_run_separate": (_i32, [_vp, _vp, ctypes.POINTER(_u64),
+                                         ctypes.POINTER(ctypes.c_float)]),
+        "nq_batch_counts": (_i32, [_vp, _i32, _vp, _u64, ctypes.POINTER(_u64)]),
+        "nq_batch_destroy": (None, [_vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -115,10 +125,11 @@ def _stream_handle(stream) -> int | None:
     return stream.cuda_stream
 
 
-def make_config(layout=0, block=0, blocks_per_sm=0, order=0, d=0) -> Config:
+def make_config(layout=0, block=0, blocks_per_sm=0, order=0, d=0, claim=0) -> Config:
     if isinstance(layout, str):
         layout = LAYOUTS[layout]
-    return Config(int(layout), int(block), int(blocks_per_sm), int(order), int(d), (0, 0, 0))
+    return Config(int(layout), int(block), int(blocks_per_sm), int(order), int(d), int(claim),
+                  (0, 0))
 
 
 # --- host prefix generation --------------------------------------------------
@@ -242,4 +253,4 @@ def header_symbols() -> list[str]:
     import re
     path = os.path.join(_build.INCLUDE, "nq.h")
     text = open(path).read()
-    return sorted(set(re.findall(r"^\s*(?:int|const char \*)\s*(nq_\w+)\s*\(", text, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char \*)\s*(nq_\w+)\s*\(", text, re.M)))

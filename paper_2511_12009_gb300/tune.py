@@ -1,0 +1,162 @@
+"""Autotuner for the search launch.
+
+Axes: prefix depth d, stack layout, threads per block, claim order, and the
+work chunk (subproblems a lane claims per atomic). Each candidate is timed by
+the kernel's own CUDA events inside nq_total_ex (best of `reps`); every
+candidate must return the same total. The search is staged (depth, then
+layout, then block and order, then chunk), each stage keeping the best of the
+previous ones, so a board size costs a few dozen launches. Results are cached
+in a JSON file keyed by device name, SM count and board size
+(``NQ_TUNE_CACHE``, default ``paper_2511_12009_gb300/_build/tune_cache.json``).
+"""
+from __future__ import annotations
+
+import json
+import os
+import threading
+
+from . import nq
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+CACHE = os.environ.get("NQ_TUNE_CACHE", os.path.join(_HERE, "_build", "tune_cache.json"))
+_lock = threading.Lock()
+FIELDS = ("layout", "block", "blocks_per_sm", "order", "d", "claim")
+
+
+def _device_key() -> str:
+    import torch
+    p = torch.cuda.get_device_properties(torch.cuda.current_device())
+    return f"{p.name}|{p.multi_processor_count}"
+
+
+def _load() -> dict:
+    try:
+        with open(CACHE) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _store(key: str, rec: dict):
+    with _lock:
+        data = _load()
+        data[key] = rec
+        os.makedirs(os.path.dirname(CACHE), exist_ok=True)
+        tmp = CACHE + f".{os.getpid()}.tmp"
+        with open(tmp, "w") as f:
+            json.dump(data, f, indent=1, sort_keys=True)
+        os.replace(tmp, CACHE)
+
+
+def measure(n: int, cfg: dict, reps: int = 2) -> tuple[float, int]:
+    """Best kernel milliseconds of nq_total_ex over `reps` runs, and the total."""
+    best, total = None, None
+    c = nq.make_config(**cfg)
+    for _ in range(reps):
+        r = nq.total_ex(n, c)
+        if total is not None and r["total"] != total:
+            raise RuntimeError(f"N={n}: totals differ between runs of {cfg}")
+        total = r["total"]
+        best = r["kernel_ms"] if best is None else min(best, r["kernel_ms"])
+    return best, total
+
+
+def _depths(n: int, max_records: int) -> list[int]:
+    d0 = nq.default_depth(n)
+    out = []
+    for d in (d0 - 1, d0, d0 + 1):
+        if 1 <= d <= max(1, n - 2) and nq.prefix_count(n, d) <= max_records:
+            out.append(d)
+    return out or [d0]
+
+
+def tune(n: int, reps: int = 2, max_records: int = 64_000_000, layouts=("regm", "reg", "wt"),
+         blocks=(128, 256, 512), claims=(1, 2, 4), verbose=False) -> dict:
+    """Tune the launch for board size n; returns the best config (also cached)."""
+    key = f"{_device_key()}|N={n}"
+    tried = []
+
+    def run(cfg):
+        ms, total = measure(n, cfg, reps)
+        tried.append({**cfg, "ms": ms})
+        if verbose:
+            print(f"  N={n} {cfg} -> {ms:.3f} ms", flush=True)
+        return ms, total
+
+    best = {"layout": 0, "block": 0, "blocks_per_sm": 0, "order": 0, "d": nq.default_depth(n),
+            "claim": 0}
+    best_ms, ref_total = run(best)
+
+    def stage(variants):
+        nonlocal best, best_ms
+        for change in variants:
+            cfg = {**best, **change}
+            if cfg == best:
+                continue
+            ms, total = run(cfg)
+            if total != ref_total:
+                raise RuntimeError(f"N={n}: {cfg} gives {total}, expected {ref_total}")
+            if ms < best_ms:
+                best, best_ms = cfg, ms
+
+    stage([{"d": d} for d in _depths(n, max_records)])
+    stage([{"layout": nq.LAYOUTS[lay]} for lay in layouts])
+    stage([{"block": b, "order": o} for b in blocks for o in (0, 1)])
+    stage([{"claim": c} for c in claims])
+    rec = {"config": best, "ms": best_ms, "total": ref_total, "tried": tried}
+    _store(key, rec)
+    return best
+
+
+def cached(n: int) -> dict | None:
+    rec = _load().get(f"{_device_key()}|N={n}")
+    return rec["config"] if rec else None
+
+
+def best_config(n: int) -> nq.Config:
+    """The cached tuned config for board size n, else the library defaults."""
+    cfg = cached(n)
+    return nq.make_config(**cfg) if cfg else nq.make_config(d=nq.default_depth(n))
+
+
+def tune_batch(ns, reps: int = 2, blocks=(128, 256), claims=(1, 2), verbose=False) -> dict:
+    """Tune a batched launch over boards ns: per-board depths from each board's
+    own tuning (or the default), then block size / order / chunk of the one
+    launch, timed by graph replays. Returns {"ds": [...], "config": {...}, "ms": ...}."""
+    from .batch import Batch
+    ds = []
+    for n in ns:
+        c = cached(n)
+        ds.append(c["d"] if c else nq.default_depth(n))
+    best, best_ms, ref = None, None, None
+    for layout in ("regm", "reg"):
+        for block in blocks:
+            for order in (0, 1):
+                for claim in claims:
+                    cfg = {"layout": nq.LAYOUTS[layout], "block": block, "blocks_per_sm": 0,
+                           "order": order, "d": 0, "claim": claim}
+                    with Batch(ns, ds, nq.make_config(**cfg)) as b:
+                        ms = None
+                        for _ in range(reps):
+                            tot, t = b.run()
+                            if ref is not None and tot != ref:
+                                raise RuntimeError(f"batch totals differ for {cfg}")
+                            ref = tot
+                            ms = t if ms is None else min(ms, t)
+                    if verbose:
+                        print(f"  batch {cfg} -> {ms:.3f} ms", flush=True)
+                    if best_ms is None or ms < best_ms:
+                        best, best_ms = cfg, ms
+    rec = {"ds": ds, "config": best, "ms": best_ms, "totals": ref}
+    _store(f"{_device_key()}|batch={','.join(map(str, ns))}", rec)
+    return rec
+
+
+if __name__ == "__main__":
+    import argparse
+    ap = argparse.ArgumentParser(description="tune the search launch per board size")
+    ap.add_argument("n", type=int, nargs="+")
+    ap.add_argument("--reps", type=int, default=2)
+    a = ap.parse_args()
+    for n in a.n:
+        print(n, tune(n, reps=a.reps, verbose=True))

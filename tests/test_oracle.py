@@ -244,3 +244,11 @@ def test_constrained_conflicts_and_errors(orc):
         orc.count_constrained(8, [(8, 0)])
     with pytest.raises(ValueError):
         orc.count_constrained(8, [(0, -1)])
+
+
+@pytest.mark.parametrize("n,base,rows", [(6, [], 3), (7, [1], 2), (8, [0, 2], 3), (9, [4, 0, 7], 2)])
+def test_descendants_by_brute_force(orc, n, base, rows):
+    """Extensions of a placement by `rows` rows: brute force over all column tuples."""
+    want = [tuple(base) + t for t in itertools.product(range(n), repeat=rows)
+            if _nonattacking(tuple(base) + t)]
+    assert orc.descendants(n, base, rows) == want
