@@ -264,6 +264,56 @@ int nq_batch_counts(const nq_batch *b, int board, uint64_t *h_counts, uint64_t c
 
 void nq_batch_destroy(nq_batch *b);
 
+/* ------------------------------------------------------------------------- */
+/* Serving: a request server with continuous batching (not in the paper).    */
+/* A request is a board size plus queens that must appear in the solution    */
+/* (nq_count_constrained's semantics). One persistent kernel keeps taking    */
+/* subproblems of newly admitted requests from a device ring while it is     */
+/* still searching earlier ones; the requests' counters live on the device.  */
+/* ------------------------------------------------------------------------- */
+
+typedef struct nq_server nq_server;
+
+typedef struct nq_server_config {
+    int32_t max_n;          /* largest board accepted (<= 26; 0: 20) */
+    int32_t request_slots;  /* requests in flight at once (<= 256; 0: 64) */
+    int32_t stack_slots;    /* stack frames per lane (0: 12). Admission by footprint: a
+                               request's prefix depth d is raised until N-1-d frames fit */
+    int32_t block;          /* threads per block (0: 256) */
+    uint64_t ring_records;  /* subproblem ring capacity, a power of two >= 1024 (0: 2^22) */
+    uint32_t idle_ms;       /* the kernel exits after about this long with nothing to do
+                               (bounded wait); the next submit or poll relaunches it (0: 200) */
+    int32_t reserved[3];
+} nq_server_config;
+
+/* Allocate the ring, request slots and mapped control block; no kernel runs yet. */
+int nq_server_create(const nq_server_config *cfg, nq_server **out);
+
+/*
+ * Admit one request: validate (NQ_EINVAL as nq_count_constrained), build its
+ * per-row masks and prefix rows, tag them with a free request slot, append them
+ * to the ring and publish them; (re)launch the kernel if it is not running.
+ * Returns NQ_EBUSY (nothing done) when no request slot or not enough ring space
+ * is free: poll, then retry. *ticket identifies the request in nq_server_poll.
+ * Requests whose queens conflict complete at once with count 0.
+ */
+int nq_server_submit(nq_server *s, int N, const nq_queen *q, int k, uint64_t *ticket);
+
+/*
+ * Completed requests since the last poll: up to max (ticket, count) pairs, in
+ * completion order; *n_done = how many were written. Also relaunches the kernel
+ * if it left on an idle timeout while work was being published, and returns
+ * the first error a kernel recorded.
+ */
+int nq_server_poll(nq_server *s, uint64_t *tickets, uint64_t *counts, int max, int *n_done);
+
+/* Requests submitted and completed, kernel launches, ring records published. */
+int nq_server_stats(nq_server *s, uint64_t *submitted, uint64_t *completed, uint64_t *launches,
+                    uint64_t *published);
+
+/* Ask the kernel to finish (it completes the subtrees it holds), wait, free. */
+int nq_server_destroy(nq_server *s);
+
 /*
  * Counting with no memory allocation at all (the paper has no counterpart;
  * this is a deployment aid). Some callers cannot let a library allocate: a

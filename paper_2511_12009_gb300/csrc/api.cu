@@ -238,65 +238,19 @@ extern "C" int nq_total(int N, uint64_t *total_out) {
 // prefix rows are enumerated under the same masks (no symmetry: weight 1) and
 // the constrained kernel applies the masks below the prefix.
 // ---------------------------------------------------------------------------
-namespace {
-
-struct CWalker {
-    int n, d;
-    uint32_t last;
-    const uint32_t *allowed;
-    std::vector<nq_prefix> *out;
-    void rec(int row, uint32_t cols, uint32_t ld, uint32_t rd) {
-        if (row == d) {
-            out->push_back(nq_prefix{cols, ld & last, rd, meta_of(1, n, d)});
-            return;
-        }
-        uint32_t av = last & ~(cols | ld | rd) & allowed[row];
-        while (av) {
-            const uint32_t p = av & (0u - av);
-            av ^= p;
-            rec(row + 1, cols | p, ((ld | p) << 1) & last, (rd | p) >> 1);
-        }
-    }
-};
-
-}  // namespace
-
 extern "C" int nq_count_constrained(int N, const nq_queen *q, int k, uint64_t *count_out) {
-    if (N < 1 || N > kMaxConstrainedN || k < 0 || k > 32 || (k && !q) || !count_out)
-        return NQ_EINVAL;
-    const uint32_t last = (1u << N) - 1u;
-    int fixed[32];
-    for (int r = 0; r < 32; ++r) fixed[r] = -1;
+    if (!count_out) return NQ_EINVAL;
+    uint32_t allowed[32];
     bool conflict = false;
-    for (int i = 0; i < k; ++i)
-        if (q[i].row < 0 || q[i].row >= N || q[i].col < 0 || q[i].col >= N) return NQ_EINVAL;
-    for (int i = 0; i < k; ++i) {
-        if (fixed[q[i].row] >= 0 && fixed[q[i].row] != q[i].col) conflict = true;
-        fixed[q[i].row] = q[i].col;
-    }
-    uint32_t allowed[32] = {0};
-    for (int r = 0; r < N; ++r) allowed[r] = fixed[r] >= 0 ? (1u << fixed[r]) : last;
-    for (int r0 = 0; r0 < N; ++r0) {
-        if (fixed[r0] < 0) continue;
-        const int c0 = fixed[r0];
-        for (int r = 0; r < N; ++r) {
-            if (r == r0) continue;
-            const int dr = r > r0 ? r - r0 : r0 - r;
-            uint32_t att = 1u << c0;
-            if (c0 + dr < N) att |= 1u << (c0 + dr);
-            if (c0 - dr >= 0) att |= 1u << (c0 - dr);
-            allowed[r] &= ~att;
-            if (fixed[r] >= 0 && !allowed[r]) conflict = true;  // listed queens attack
-        }
-    }
+    const int rc0 = constraint_masks(N, q, k, allowed, &conflict);
+    if (rc0) return rc0;
     if (conflict) {
         *count_out = 0;
         return NQ_OK;
     }
     const int d = nq_default_depth(N);
     std::vector<nq_prefix> pre;
-    CWalker w{N, d, last, allowed, &pre};
-    w.rec(0, 0, 0, 0);
+    constrained_prefixes(N, d, allowed, 0, pre);
     if (pre.empty()) {
         *count_out = 0;
         return NQ_OK;

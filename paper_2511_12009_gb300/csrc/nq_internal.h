@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "nq.h"
 
 namespace nqi {
@@ -34,6 +36,54 @@ struct SearchArgs {
 constexpr int kRowShift = 27;
 constexpr int kMaxConstrainedN = 26;
 
+// ---------------------------------------------------------------------------
+// Served mode: a persistent kernel fed through a device ring.
+// ---------------------------------------------------------------------------
+
+// One request slot's parameters, written by the host before the request's
+// records are published; read by the kernel (bypassing L1) at claim time.
+struct ServeSlot {
+    uint32_t allowed[32];  // columns each row may take (0 for rows >= N)
+    uint32_t n;            // board size
+    uint32_t gen;          // bumped on every reuse of the slot
+    uint64_t seq;          // the request's ticket
+};
+
+// Host-visible control block (mapped pinned memory).
+struct ServeControl {
+    volatile unsigned long long head;   // records published (host writes)
+    volatile int stop;                  // host asks the kernel to finish
+    volatile int exit_reason;           // kernel: 1 stopped, 2 idle timeout
+};
+
+// Completion record of a request slot (mapped pinned memory, written by the
+// lane that finishes the slot's last subproblem).
+struct ServeDone {
+    volatile unsigned long long total;
+    volatile unsigned long long seq;
+};
+
+constexpr int kServeMaxSlots = 256;
+
+struct ServeArgs {
+    const nq_prefix *ring;           // ring_mask + 1 records (device)
+    unsigned long long ring_mask;
+    unsigned long long *cursor;      // next index to claim (device)
+    ServeControl *ctl;               // mapped
+    const ServeSlot *slot_info;      // [nslots] (device)
+    unsigned long long *slot_total;  // [nslots] (device)
+    unsigned int *slot_remaining;    // [nslots] (device)
+    ServeDone *done;                 // [nslots] (mapped)
+    int nslots;
+    int slots;                       // stack slots per lane
+    unsigned int idle_polls;         // empty polls (with back-off) before exiting
+    uint32_t mul[4];                 // as in SearchArgs
+};
+
+int launch_serve(const ServeArgs &a, int grid, int block, size_t smem, cudaStream_t s);
+int serve_plan(int max_n, int min_d, int nslots, int block, int *grid, size_t *smem,
+               int *slots);
+
 // A resolved launch shape.
 struct Plan {
     int layout;     // NQ_LAYOUT_PAPER / NQ_LAYOUT_REG
@@ -59,5 +109,11 @@ int take_device_status();
 
 // Host enumeration helpers (prefix.cpp).
 uint32_t meta_of(int weight, int n, int d);
+
+// Partial-board constraints (constrain.cpp): per-row allowed masks (rows >= N
+// zero) and whether the listed queens conflict; the prefix rows under them.
+int constraint_masks(int N, const nq_queen *q, int k, uint32_t allowed[32], bool *conflict);
+void constrained_prefixes(int N, int d, const uint32_t allowed[32], uint32_t tag,
+                          std::vector<nq_prefix> &out);
 
 }  // namespace nqi

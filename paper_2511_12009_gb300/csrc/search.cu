@@ -599,6 +599,179 @@ __global__ void __maxnreg__(48) search_kernel(const SearchArgs a) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Served mode: one persistent launch that keeps taking subproblems of newly
+// admitted requests from a device ring while earlier ones are still being
+// searched (continuous batching). Each record's tag names its request slot;
+// the slot's allowed-column masks are cached per block in shared memory and
+// refreshed by generation number. The lane that finishes a slot's last
+// subproblem publishes the slot's total to mapped host memory. Every wait is
+// bounded: the claim retries a fixed number of times, and a warp with nothing
+// to do polls the ring at most idle_polls times (with back-off) before it
+// exits, so the kernel always ends by itself once the host stops feeding it.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 ld_cg4(const void *p) {
+    uint4 v;
+    asm volatile("ld.global.cg.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p)
+                 : "memory");
+    return v;
+}
+__device__ __forceinline__ uint32_t ld_cg1(const void *p) {
+    uint32_t v;
+    asm volatile("ld.global.cg.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__global__ void __maxnreg__(64) serve_kernel(const ServeArgs a) {
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(nq_smem);
+    Lane k;
+    k.stride = blockDim.x * 16u;
+    k.base = sbase + threadIdx.x * 16u;
+    k.limit = k.base + (uint32_t)a.slots * k.stride;
+    const uint32_t tables = sbase + (uint32_t)a.slots * k.stride;   // nslots x 128 B
+    const uint32_t gens = tables + (uint32_t)a.nslots * 128u;        // nslots x 4 B
+    k.table = tables;
+    k.thr = 0;
+    for (int i = threadIdx.x; i < a.nslots; i += blockDim.x) sts1(gens + 4u * i, 0xFFFFFFFFu);
+    for (int i = threadIdx.x; i < a.nslots * 32; i += blockDim.x) sts1(tables + 4u * i, 0u);
+    __syncthreads();
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned lt_mask = (1u << lane) - 1u;
+
+    uint32_t c = kSentinelC, l = ~0u, r = ~0u, av = kSentinelAvC;
+    uint32_t top = k.base;
+    sts4(k.base, make_uint4(kSentinelC, ~0u, ~0u, kSentinelAvC));
+    int cur_slot = -1;
+    uint64_t sol = 0;
+    unsigned int idle_polls = 0;
+
+    auto finish_slot = [&](int slot, uint64_t s) {
+        if (s) atomicAdd(&a.slot_total[slot], (unsigned long long)s);
+        __threadfence();
+        if (atomicSub(&a.slot_remaining[slot], 1u) == 1u) {
+            __threadfence();
+            const unsigned long long tot = atomicAdd(&a.slot_total[slot], 0ull);
+            const unsigned long long seq = *reinterpret_cast<const volatile unsigned long long *>(
+                &a.slot_info[slot].seq);
+            a.done[slot].total = tot;
+            __threadfence_system();
+            a.done[slot].seq = seq;
+            __threadfence_system();
+        }
+    };
+
+    for (;;) {
+        const bool idle = top == k.base;
+        if (idle) {
+            if (cur_slot >= 0) {
+                finish_slot(cur_slot, sol);
+                cur_slot = -1;
+            }
+            c = kSentinelC;
+            l = r = ~0u;
+            av = kSentinelAvC;
+        }
+        bool need = idle;
+        unsigned need_mask = __ballot_sync(~0u, need);
+        bool stopping = false;
+        if (need_mask) {  // one read of the mapped flag per warp
+            int st = 0;
+            if (lane == 0) st = a.ctl->stop;
+            stopping = __shfl_sync(~0u, st, 0) != 0;
+        }
+        while (need_mask && !stopping) {
+            const int leader = __ffs(need_mask) - 1;
+            unsigned long long first = 0, got = 0;
+            if ((int)lane == leader) {
+                const unsigned long long h = a.ctl->head;
+                unsigned long long cur = atomicAdd(a.cursor, 0ull);
+                for (int t = 0; t < 64 && cur < h; ++t) {
+                    const unsigned long long want =
+                        h - cur < (unsigned long long)__popc(need_mask) ? h - cur
+                                                                       : (unsigned long long)__popc(need_mask);
+                    const unsigned long long old = atomicCAS(a.cursor, cur, cur + want);
+                    if (old == cur) {
+                        first = cur;
+                        got = want;
+                        break;
+                    }
+                    cur = old;
+                }
+                __threadfence();  // records published before head are visible
+            }
+            first = __shfl_sync(~0u, first, leader);
+            got = __shfl_sync(~0u, got, leader);
+            if (got == 0) break;
+            const unsigned rank = __popc(need_mask & lt_mask);
+            if (need && rank < got) {
+                const unsigned long long idx = first + rank;
+                const uint4 P = ld_cg4(a.ring + (idx & a.ring_mask));
+                const uint32_t n = (P.w >> 2) & 31u, d = (P.w >> 7) & 31u;
+                const int slot = (int)(P.w >> 12);
+                const uint32_t last = (n >= 1u) ? (0xFFFFFFFFu >> (32u - n)) : 0u;
+                const bool ok = slot < a.nslots && n >= 1u && n <= (uint32_t)kMaxConstrainedN &&
+                                d <= n && (P.x & ~last) == 0u && (uint32_t)__popc(P.x) == d &&
+                                (d + 1u >= n || (int)n - 1 - (int)d <= a.slots);
+                if (!ok) {
+                    record_error(NQ_EINVAL);
+                    if (slot < a.nslots) finish_slot(slot, 0);
+                } else {
+                    // the slot's allowed masks, cached in this block's shared memory
+                    const uint32_t gen = ld_cg1(&a.slot_info[slot].gen);
+                    const uint32_t tab = tables + 128u * (uint32_t)slot;
+                    __threadfence_block();
+                    if (lds1(gens + 4u * slot) != gen) {
+                        for (int w = 0; w < 32; ++w)
+                            sts1(tab + 4u * w, ld_cg1(&a.slot_info[slot].allowed[w]));
+                        __threadfence_block();
+                        sts1(gens + 4u * slot, gen);
+                    }
+                    const uint32_t l0 = P.y;
+                    const uint32_t r0 = P.z & last;
+                    const uint32_t c0 = P.x | (d << kRowShift);
+                    const uint32_t a0 = ~(c0 | l0 | r0) & lds1(tab + (d << 2)) & last;
+                    if (d == n) {
+                        finish_slot(slot, 1);
+                    } else if (d + 1u == n || a0 == 0u) {
+                        finish_slot(slot, (uint64_t)__popc(a0));
+                    } else {
+                        cur_slot = slot;
+                        sol = 0;
+                        k.table = tab;
+                        k.thr = (n - 1u) << kRowShift;
+                        c = c0; l = l0; r = r0; av = a0;
+                        top = k.base + k.stride;
+                        need = false;
+                    }
+                }
+            }
+            const unsigned asked = __popc(need_mask);
+            need_mask = __ballot_sync(~0u, need);
+            if (got < asked) break;  // the ring is drained for now
+        }
+        if (__all_sync(~0u, top == k.base && cur_slot < 0)) {
+            // (plain stores to the mapped block: no atomics on host memory)
+            if (stopping) {
+                if (lane == 0) a.ctl->exit_reason = 1;
+                break;
+            }
+            if (++idle_polls > a.idle_polls) {
+                if (lane == 0) a.ctl->exit_reason = 2;
+                break;
+            }
+            __nanosleep(idle_polls < 64 ? 256u : 4096u);
+            continue;
+        }
+        idle_polls = 0;
+        uint32_t s32 = 0, n32 = 0;
+#pragma unroll
+        for (int j = 0; j < kChunk; ++j) step_reg<false, true>(c, l, r, av, top, k, s32, n32);
+        sol += s32;
+    }
+}
+
 template <int LAYOUT, bool DIAG, bool CONSTR>
 void *kernel_ptr() {
     return reinterpret_cast<void *>(&search_kernel<LAYOUT, DIAG, CONSTR>);
@@ -685,6 +858,42 @@ int launch_search(const SearchArgs &a, const Plan &p, bool diag, bool constraine
     SearchArgs args = a;
     void *params[] = {&args};
     const cudaError_t e = cudaLaunchKernel(k, dim3(p.grid), dim3(p.block), params, p.smem, s);
+    return e == cudaSuccess ? NQ_OK : NQ_ECUDA;
+}
+
+int serve_plan(int max_n, int min_d, int nslots, int block, int *grid, size_t *smem,
+               int *slots) {
+    if (max_n < 1 || max_n > kMaxConstrainedN || min_d < 0 || min_d > max_n || nslots < 1 ||
+        nslots > kServeMaxSlots || block < 32 || block > 1024 || block % 32)
+        return NQ_EINVAL;
+    int dev = 0, sms = 0, max_smem = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
+            cudaSuccess)
+        return NQ_ECUDA;
+    const int sl = slots_needed(NQ_LAYOUT_REG, max_n, min_d);
+    const size_t bytes = (size_t)sl * 16u * block + (size_t)nslots * 132u;
+    if (bytes > (size_t)max_smem) return NQ_ESTACK;
+    void *k = reinterpret_cast<void *>(&serve_kernel);
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+        cudaSuccess)
+        return NQ_ECUDA;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, bytes) != cudaSuccess)
+        return NQ_ECUDA;
+    if (nb < 1) return NQ_ESTACK;
+    *grid = sms * nb;
+    *smem = bytes;
+    *slots = sl;
+    return NQ_OK;
+}
+
+int launch_serve(const ServeArgs &a, int grid, int block, size_t smem, cudaStream_t s) {
+    ServeArgs args = a;
+    void *params[] = {&args};
+    const cudaError_t e = cudaLaunchKernel(reinterpret_cast<void *>(&serve_kernel), dim3(grid),
+                                           dim3(block), params, smem, s);
     return e == cudaSuccess ? NQ_OK : NQ_ECUDA;
 }
 

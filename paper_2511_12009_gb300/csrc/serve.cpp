@@ -1,0 +1,317 @@
+// serve.cpp -- continuous-batching request server around serve_kernel.
+//
+// A request (board size N plus queens that must appear in the solution) is
+// compiled on the host into per-row allowed masks and the prefix rows
+// enumerated under them, tagged with a free request slot, appended to the
+// device ring and published by advancing the ring's head in mapped memory.
+// The persistent kernel picks the new subproblems up while it is still
+// searching older ones. Admission: a request is taken only when a slot is
+// free, the ring has room (ring positions are reused only below the end of
+// the latest completed request: claims are in ring order, so everything
+// below it has been read), and its stack footprint fits the running kernel's
+// (its prefix depth is raised until N - 1 - d frames fit).
+#include <algorithm>
+#include <atomic>
+#include <deque>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "nq_internal.h"
+
+using nqi::ServeControl;
+using nqi::ServeDone;
+using nqi::ServeSlot;
+
+struct nq_server {
+    nq_server_config cfg{};
+    int dev = 0;
+    int grid = 0, block = 0, stack_slots = 0, min_d = 0;
+    size_t smem = 0;
+    uint64_t ring = 0, mask = 0;
+    cudaStream_t kstream = nullptr, cstream = nullptr;
+    cudaEvent_t kdone = nullptr;
+    bool launched = false;
+    nq_prefix *d_ring = nullptr;
+    unsigned long long *d_cursor = nullptr;
+    ServeSlot *d_slot = nullptr;
+    unsigned long long *d_total = nullptr;
+    unsigned int *d_remaining = nullptr;
+    ServeControl *h_ctl = nullptr, *d_ctl = nullptr;
+    ServeDone *h_done = nullptr, *d_done = nullptr;
+    uint64_t head = 0;       // records published
+    uint64_t consumed = 0;   // every index below has been claimed
+    uint64_t next_ticket = 1;
+    uint64_t launches = 0, submitted = 0, completed = 0;
+    struct Req {
+        uint64_t ticket = 0, end = 0;
+        bool active = false;
+    };
+    std::vector<Req> req;
+    std::vector<uint32_t> gen;
+    std::deque<std::pair<uint64_t, uint64_t>> ready;
+    std::mutex mu;
+};
+
+namespace {
+
+void release(nq_server *s) {
+    if (!s) return;
+    if (s->kstream) cudaStreamSynchronize(s->kstream);
+    if (s->d_ring) cudaFree(s->d_ring);
+    if (s->d_cursor) cudaFree(s->d_cursor);
+    if (s->d_slot) cudaFree(s->d_slot);
+    if (s->d_total) cudaFree(s->d_total);
+    if (s->d_remaining) cudaFree(s->d_remaining);
+    if (s->h_ctl) cudaFreeHost(s->h_ctl);
+    if (s->h_done) cudaFreeHost(s->h_done);
+    if (s->kdone) cudaEventDestroy(s->kdone);
+    if (s->kstream) cudaStreamDestroy(s->kstream);
+    if (s->cstream) cudaStreamDestroy(s->cstream);
+    delete s;
+}
+
+// (Re)launch the persistent kernel if none is running. Caller holds mu.
+int ensure_running(nq_server *s) {
+    if (s->launched) {
+        const cudaError_t q = cudaEventQuery(s->kdone);
+        if (q == cudaErrorNotReady) return NQ_OK;
+        if (q != cudaSuccess) return NQ_ECUDA;
+    }
+    s->h_ctl->stop = 0;
+    s->h_ctl->exit_reason = 0;
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    nqi::ServeArgs a{};
+    a.ring = s->d_ring;
+    a.ring_mask = s->mask;
+    a.cursor = s->d_cursor;
+    a.ctl = s->d_ctl;
+    a.slot_info = s->d_slot;
+    a.slot_total = s->d_total;
+    a.slot_remaining = s->d_remaining;
+    a.done = s->d_done;
+    a.nslots = s->cfg.request_slots;
+    a.slots = s->stack_slots;
+    // about idle_ms of polling: the back-off sleeps 4 us per poll once idle
+    a.idle_polls = 64u + s->cfg.idle_ms * 250u;
+    a.mul[0] = 1u;
+    a.mul[1] = 2u;
+    a.mul[2] = 0xFFFFFFFFu;
+    a.mul[3] = 0x80000000u;
+    int rc = nqi::launch_serve(a, s->grid, s->block, s->smem, s->kstream);
+    if (rc) return rc;
+    if (cudaEventRecord(s->kdone, s->kstream) != cudaSuccess) return NQ_ECUDA;
+    s->launched = true;
+    ++s->launches;
+    return NQ_OK;
+}
+
+// Collect finished requests. Caller holds mu.
+void collect(nq_server *s) {
+    for (size_t i = 0; i < s->req.size(); ++i) {
+        nq_server::Req &r = s->req[i];
+        if (!r.active) continue;
+        if (s->h_done[i].seq != r.ticket) continue;
+        std::atomic_thread_fence(std::memory_order_acquire);
+        s->ready.emplace_back(r.ticket, (uint64_t)s->h_done[i].total);
+        s->consumed = std::max(s->consumed, r.end);
+        r.active = false;
+        ++s->completed;
+    }
+}
+
+}  // namespace
+
+extern "C" int nq_server_create(const nq_server_config *cfg, nq_server **out) {
+    if (!cfg || !out) return NQ_EINVAL;
+    *out = nullptr;
+    nq_server_config c = *cfg;
+    if (c.max_n == 0) c.max_n = 20;
+    if (c.request_slots == 0) c.request_slots = 64;
+    if (c.stack_slots == 0) c.stack_slots = 12;
+    if (c.block == 0) c.block = 256;
+    if (c.ring_records == 0) c.ring_records = 1ull << 22;
+    if (c.idle_ms == 0) c.idle_ms = 200;
+    if (c.max_n < 1 || c.max_n > nqi::kMaxConstrainedN || c.request_slots < 1 ||
+        c.request_slots > nqi::kServeMaxSlots || c.stack_slots < 1 ||
+        c.stack_slots > c.max_n || (c.ring_records & (c.ring_records - 1)) ||
+        c.ring_records < 1024)
+        return NQ_EINVAL;
+    nq_server *s = new (std::nothrow) nq_server;
+    if (!s) return NQ_ENOMEM;
+    s->cfg = c;
+    s->ring = c.ring_records;
+    s->mask = c.ring_records - 1;
+    // stack frames per lane: REG layout needs max_n - 1 - d for depth d
+    s->min_d = std::max(0, c.max_n - 1 - c.stack_slots);
+    int rc = cudaGetDevice(&s->dev) == cudaSuccess ? NQ_OK : NQ_ECUDA;
+    if (!rc) {
+        s->block = c.block;
+        rc = nqi::serve_plan(c.max_n, s->min_d, c.request_slots, c.block, &s->grid, &s->smem,
+                             &s->stack_slots);
+    }
+    if (!rc && (cudaMalloc(&s->d_ring, s->ring * sizeof(nq_prefix)) != cudaSuccess ||
+                cudaMalloc(&s->d_cursor, sizeof(unsigned long long)) != cudaSuccess ||
+                cudaMalloc(&s->d_slot, c.request_slots * sizeof(ServeSlot)) != cudaSuccess ||
+                cudaMalloc(&s->d_total, c.request_slots * sizeof(unsigned long long)) !=
+                    cudaSuccess ||
+                cudaMalloc(&s->d_remaining, c.request_slots * sizeof(unsigned int)) !=
+                    cudaSuccess ||
+                cudaHostAlloc(&s->h_ctl, sizeof(ServeControl), cudaHostAllocMapped) !=
+                    cudaSuccess ||
+                cudaHostAlloc(&s->h_done, c.request_slots * sizeof(ServeDone),
+                              cudaHostAllocMapped) != cudaSuccess))
+        rc = NQ_ENOMEM;
+    if (!rc && (cudaHostGetDevicePointer(&s->d_ctl, s->h_ctl, 0) != cudaSuccess ||
+                cudaHostGetDevicePointer(&s->d_done, s->h_done, 0) != cudaSuccess ||
+                cudaStreamCreateWithFlags(&s->kstream, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaStreamCreateWithFlags(&s->cstream, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&s->kdone, cudaEventDisableTiming) != cudaSuccess ||
+                cudaMemset(s->d_cursor, 0, sizeof(unsigned long long)) != cudaSuccess ||
+                cudaMemset(s->d_slot, 0, c.request_slots * sizeof(ServeSlot)) != cudaSuccess))
+        rc = NQ_ECUDA;
+    if (rc) {
+        release(s);
+        return rc;
+    }
+    s->h_ctl->head = 0;
+    s->h_ctl->stop = 0;
+    s->h_ctl->exit_reason = 0;
+    for (int i = 0; i < c.request_slots; ++i) {
+        s->h_done[i].seq = 0;
+        s->h_done[i].total = 0;
+    }
+    s->req.resize(c.request_slots);
+    s->gen.assign(c.request_slots, 0);
+    *out = s;
+    return NQ_OK;
+}
+
+extern "C" int nq_server_submit(nq_server *s, int N, const nq_queen *q, int k, uint64_t *ticket) {
+    if (!s || !ticket) return NQ_EINVAL;
+    std::lock_guard<std::mutex> guard(s->mu);
+    if (N < 1 || N > s->cfg.max_n) return NQ_EINVAL;
+    uint32_t allowed[32];
+    bool conflict = false;
+    int rc = nqi::constraint_masks(N, q, k, allowed, &conflict);
+    if (rc) return rc;
+    collect(s);
+    if (conflict) {  // no solution contains both queens
+        *ticket = s->next_ticket++;
+        s->ready.emplace_back(*ticket, 0);
+        ++s->submitted;
+        ++s->completed;
+        return NQ_OK;
+    }
+    int slot = -1;
+    for (int i = 0; i < (int)s->req.size(); ++i)
+        if (!s->req[i].active) {
+            slot = i;
+            break;
+        }
+    if (slot < 0) return NQ_EBUSY;
+    // the request's depth: at least what fits the kernel's stack, at most N
+    const int d = std::min(N, std::max(N - 1 - s->stack_slots, std::min(N - 2 < 0 ? 0 : N - 2, 5)));
+    std::vector<nq_prefix> pre;
+    nqi::constrained_prefixes(N, d, allowed, (uint32_t)slot, pre);
+    const uint64_t m = pre.size();
+    const uint64_t tk = s->next_ticket;
+    if (m == 0) {
+        *ticket = s->next_ticket++;
+        s->ready.emplace_back(*ticket, 0);
+        ++s->submitted;
+        ++s->completed;
+        return NQ_OK;
+    }
+    if (m > s->ring) return NQ_EOVERFLOW;
+    if (s->head + m - s->consumed > s->ring) return NQ_EBUSY;
+    // slot parameters, its counters, then the records (possibly wrapping)
+    ServeSlot info{};
+    for (int r = 0; r < 32; ++r) info.allowed[r] = allowed[r];
+    info.n = (uint32_t)N;
+    info.gen = ++s->gen[slot];
+    info.seq = tk;
+    const unsigned long long zero = 0;
+    const unsigned int rem = (unsigned int)m;
+    bool ok = cudaMemcpyAsync(&s->d_slot[slot], &info, sizeof(info), cudaMemcpyHostToDevice,
+                              s->cstream) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(&s->d_total[slot], &zero, sizeof(zero), cudaMemcpyHostToDevice,
+                               s->cstream) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(&s->d_remaining[slot], &rem, sizeof(rem), cudaMemcpyHostToDevice,
+                               s->cstream) == cudaSuccess;
+    const uint64_t pos = s->head & s->mask;
+    const uint64_t first_part = std::min(m, s->ring - pos);
+    ok = ok && cudaMemcpyAsync(s->d_ring + pos, pre.data(), first_part * sizeof(nq_prefix),
+                               cudaMemcpyHostToDevice, s->cstream) == cudaSuccess;
+    if (first_part < m)
+        ok = ok && cudaMemcpyAsync(s->d_ring, pre.data() + first_part,
+                                   (m - first_part) * sizeof(nq_prefix), cudaMemcpyHostToDevice,
+                                   s->cstream) == cudaSuccess;
+    ok = ok && cudaStreamSynchronize(s->cstream) == cudaSuccess;
+    if (!ok) return NQ_ECUDA;
+    // publish
+    s->head += m;
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    s->h_ctl->head = s->head;
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    s->req[slot].ticket = tk;
+    s->req[slot].end = s->head;
+    s->req[slot].active = true;
+    s->next_ticket++;
+    ++s->submitted;
+    *ticket = tk;
+    return ensure_running(s);
+}
+
+extern "C" int nq_server_poll(nq_server *s, uint64_t *tickets, uint64_t *counts, int max,
+                              int *n_done) {
+    if (!s || !n_done || max < 0 || (max && (!tickets || !counts))) return NQ_EINVAL;
+    std::lock_guard<std::mutex> guard(s->mu);
+    collect(s);
+    bool pending = false;
+    for (const auto &r : s->req) pending = pending || r.active;
+    int rc = NQ_OK;
+    if (s->launched) {
+        const cudaError_t q = cudaEventQuery(s->kdone);
+        if (q != cudaSuccess && q != cudaErrorNotReady) return NQ_ECUDA;
+        // the kernel left (idle) while work was being published: start it again
+        if (q == cudaSuccess && pending) rc = ensure_running(s);
+        if (q == cudaSuccess) {
+            const int st = nqi::take_device_status();
+            if (st && !rc) rc = st;
+        }
+    }
+    int n = 0;
+    while (n < max && !s->ready.empty()) {
+        tickets[n] = s->ready.front().first;
+        counts[n] = s->ready.front().second;
+        s->ready.pop_front();
+        ++n;
+    }
+    *n_done = n;
+    return rc;
+}
+
+extern "C" int nq_server_stats(nq_server *s, uint64_t *submitted, uint64_t *completed,
+                               uint64_t *launches, uint64_t *published) {
+    if (!s) return NQ_EINVAL;
+    std::lock_guard<std::mutex> guard(s->mu);
+    if (submitted) *submitted = s->submitted;
+    if (completed) *completed = s->completed;
+    if (launches) *launches = s->launches;
+    if (published) *published = s->head;
+    return NQ_OK;
+}
+
+extern "C" int nq_server_destroy(nq_server *s) {
+    if (!s) return NQ_EINVAL;
+    int rc = NQ_OK;
+    {
+        std::lock_guard<std::mutex> guard(s->mu);
+        s->h_ctl->stop = 1;
+        std::atomic_thread_fence(std::memory_order_seq_cst);
+        if (s->launched && cudaStreamSynchronize(s->kstream) != cudaSuccess) rc = NQ_ECUDA;
+    }
+    release(s);
+    return rc;
+}
