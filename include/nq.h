@@ -280,7 +280,7 @@ typedef struct nq_server_config {
     int32_t stack_slots;    /* stack frames per lane (0: 12). Admission by footprint: a
                                request's prefix depth d is raised until N-1-d frames fit */
     int32_t block;          /* threads per block (0: 256) */
-    uint64_t ring_records;  /* subproblem ring capacity, a power of two >= 1024 (0: 2^22) */
+    uint64_t ring_records;  /* subproblem ring capacity, a power of two >= 1024 (0: 2^25) */
     uint32_t idle_ms;       /* the kernel exits after about this long with nothing to do
                                (bounded wait); the next submit or poll relaunches it (0: 200) */
     int32_t reserved[3];
@@ -295,7 +295,8 @@ int nq_server_create(const nq_server_config *cfg, nq_server **out);
  * to the ring and publish them; (re)launch the kernel if it is not running.
  * Returns NQ_EBUSY (nothing done) when no request slot or not enough ring space
  * is free: poll, then retry. *ticket identifies the request in nq_server_poll.
- * Requests whose queens conflict complete at once with count 0.
+ * Requests whose queens conflict complete at once with count 0. A request with
+ * no queens uses the symmetric prefix set of Section 1 (weighted counts).
  */
 int nq_server_submit(nq_server *s, int N, const nq_queen *q, int k, uint64_t *ticket);
 

@@ -644,6 +644,7 @@ __global__ void __maxnreg__(64) serve_kernel(const ServeArgs a) {
     uint32_t top = k.base;
     sts4(k.base, make_uint4(kSentinelC, ~0u, ~0u, kSentinelAvC));
     int cur_slot = -1;
+    uint32_t cur_w = 1;  // symmetry weight of the record being searched
     uint64_t sol = 0;
     unsigned int idle_polls = 0;
 
@@ -666,7 +667,7 @@ __global__ void __maxnreg__(64) serve_kernel(const ServeArgs a) {
         const bool idle = top == k.base;
         if (idle) {
             if (cur_slot >= 0) {
-                finish_slot(cur_slot, sol);
+                finish_slot(cur_slot, sol * cur_w);
                 cur_slot = -1;
             }
             c = kSentinelC;
@@ -708,10 +709,11 @@ __global__ void __maxnreg__(64) serve_kernel(const ServeArgs a) {
             if (need && rank < got) {
                 const unsigned long long idx = first + rank;
                 const uint4 P = ld_cg4(a.ring + (idx & a.ring_mask));
-                const uint32_t n = (P.w >> 2) & 31u, d = (P.w >> 7) & 31u;
+                const uint32_t n = (P.w >> 2) & 31u, d = (P.w >> 7) & 31u, w = P.w & 3u;
                 const int slot = (int)(P.w >> 12);
                 const uint32_t last = (n >= 1u) ? (0xFFFFFFFFu >> (32u - n)) : 0u;
                 const bool ok = slot < a.nslots && n >= 1u && n <= (uint32_t)kMaxConstrainedN &&
+                                (w == 1u || w == 2u) &&
                                 d <= n && (P.x & ~last) == 0u && (uint32_t)__popc(P.x) == d &&
                                 (d + 1u >= n || (int)n - 1 - (int)d <= a.slots);
                 if (!ok) {
@@ -733,11 +735,12 @@ __global__ void __maxnreg__(64) serve_kernel(const ServeArgs a) {
                     const uint32_t c0 = P.x | (d << kRowShift);
                     const uint32_t a0 = ~(c0 | l0 | r0) & lds1(tab + (d << 2)) & last;
                     if (d == n) {
-                        finish_slot(slot, 1);
+                        finish_slot(slot, w);
                     } else if (d + 1u == n || a0 == 0u) {
-                        finish_slot(slot, (uint64_t)__popc(a0));
+                        finish_slot(slot, (uint64_t)__popc(a0) * w);
                     } else {
                         cur_slot = slot;
+                        cur_w = w;
                         sol = 0;
                         k.table = tab;
                         k.thr = (n - 1u) << kRowShift;

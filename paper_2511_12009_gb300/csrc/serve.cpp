@@ -130,7 +130,7 @@ extern "C" int nq_server_create(const nq_server_config *cfg, nq_server **out) {
     if (c.request_slots == 0) c.request_slots = 64;
     if (c.stack_slots == 0) c.stack_slots = 12;
     if (c.block == 0) c.block = 256;
-    if (c.ring_records == 0) c.ring_records = 1ull << 22;
+    if (c.ring_records == 0) c.ring_records = 1ull << 25;
     if (c.idle_ms == 0) c.idle_ms = 200;
     if (c.max_n < 1 || c.max_n > nqi::kMaxConstrainedN || c.request_slots < 1 ||
         c.request_slots > nqi::kServeMaxSlots || c.stack_slots < 1 ||
@@ -213,7 +213,17 @@ extern "C" int nq_server_submit(nq_server *s, int N, const nq_queen *q, int k, u
     // the request's depth: at least what fits the kernel's stack, at most N
     const int d = std::min(N, std::max(N - 1 - s->stack_slots, std::min(N - 2 < 0 ? 0 : N - 2, 5)));
     std::vector<nq_prefix> pre;
-    nqi::constrained_prefixes(N, d, allowed, (uint32_t)slot, pre);
+    if (k == 0) {
+        // no queen given: the symmetric prefix set of Section 1 (weights 1 or 2)
+        uint64_t np = 0;
+        int erc = nq_enumerate_prefixes(N, d, nullptr, 0, &np);
+        if (erc) return erc;
+        pre.resize(np);
+        if (np && (erc = nq_enumerate_prefixes(N, d, pre.data(), np, &np))) return erc;
+        for (auto &p : pre) p.meta |= (uint32_t)slot << 12;
+    } else {
+        nqi::constrained_prefixes(N, d, allowed, (uint32_t)slot, pre);
+    }
     const uint64_t m = pre.size();
     const uint64_t tk = s->next_ticket;
     if (m == 0) {
