@@ -109,7 +109,9 @@ typedef struct nq_config {
                               1 index order, 2 last index first */
     int32_t d;             /* nq_total_ex only: prefix depth 1..N (0 = default) */
     int32_t claim;         /* subproblems a lane claims per atomic (work chunk), 1..64 */
-    int32_t reserved[2];
+    int32_t donate;        /* subtree donation once the queue is empty (register
+                              layouts): 0 default (off), 1 off, 2 on */
+    int32_t reserved;
 } nq_config;
 
 /* Timing of one nq_total_ex call, host wall clock in milliseconds. */
@@ -213,6 +215,31 @@ int nq_total(int N, uint64_t *total_out);
  */
 int nq_total_ex(int N, const nq_config *cfg, uint64_t *total_out, uint64_t *nodes_out,
                 nq_timing *timing);
+
+/*
+ * Count host-resident subproblems after splitting them on the host: each
+ * prefix is extended by `rows` more rows (every placement; the children keep
+ * the parent's weight and carry the parent's index in the tag field), the
+ * children are searched in one launch, and each child's count and nodes are
+ * added into its parent's entry. A prefix's subtree is the disjoint union of
+ * its children's subtrees (Section 1), so the results equal nq_count_ex on
+ * the prefixes themselves; the split restores load balance when there are
+ * few heavy subproblems (fewer than the grid has lanes). Synchronous.
+ *   h_prefixes [n] host records, any board sizes, n <= 2^20 (the tag width)
+ *   rows       rows to add (capped at N - d per record); -1 = the fewest rows
+ *              giving at least 32 children per resident lane of the launch
+ *   cfg        optional launch configuration (cfg->d and cfg->donate unused)
+ *   h_counts   [n] out: solutions below each prefix (raw, no weight)
+ *   h_nodes    optional [n] out: search nodes below each prefix (placements in
+ *              rows d..N-1, as nq_count_ex; runs the diagnostic build)
+ *   h_totals   optional [32] out (overwritten): weight x solutions per N
+ *   rows_used  optional out: the rows added
+ *   timing     optional: enumerate_ms = host split, prefixes = children
+ * More than 2^27 children is NQ_EOVERFLOW; malformed records NQ_EINVAL.
+ */
+int nq_count_split(const nq_prefix *h_prefixes, uint64_t n, int rows, const nq_config *cfg,
+                   uint64_t *h_counts, uint64_t *h_nodes, uint64_t *h_totals, int *rows_used,
+                   nq_timing *timing);
 
 /*
  * Solutions of the N x N board that contain every listed queen (partial-board

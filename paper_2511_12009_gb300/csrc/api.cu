@@ -1,4 +1,5 @@
 // api.cu -- the extern "C" entry points of libnq (declared in include/nq.h).
+#include <algorithm>
 #include <chrono>
 #include <cstring>
 #include <memory>
@@ -66,10 +67,19 @@ struct CallCtx {
 };
 
 // Enqueue one search over device-resident prefixes (shared by nq_count*,
-// nq_total_ex and nq_count_constrained).
+// nq_total_ex, nq_count_constrained and nq_count_split). n_tags > 0: the
+// records are split subproblems whose counts and nodes are added into entry
+// tag of d_counts / d_nodes (zeroed here, n_tags entries).
 int enqueue_search(const nq_prefix *d_prefixes, uint64_t n, int expect_n, int min_d, int max_n,
                    uint64_t *d_counts, uint64_t *d_nodes, uint64_t *d_totals,
-                   const nq_config *cfg, const uint32_t *allowed, cudaStream_t s, Plan *used) {
+                   const nq_config *cfg, const uint32_t *allowed, cudaStream_t s, Plan *used,
+                   uint64_t n_tags = 0) {
+    if (n_tags && !d_counts) return NQ_EINVAL;
+    if (n_tags) {
+        if (cudaMemsetAsync(d_counts, 0, n_tags * sizeof(uint64_t), s) != cudaSuccess ||
+            (d_nodes && cudaMemsetAsync(d_nodes, 0, n_tags * sizeof(uint64_t), s) != cudaSuccess))
+            return NQ_ECUDA;
+    }
     if (n == 0) return NQ_OK;
     if (!d_prefixes || !aligned(d_prefixes, 16) || (d_counts && !aligned(d_counts, 8)) ||
         (d_nodes && !aligned(d_nodes, 8)) || (d_totals && !aligned(d_totals, 8)))
@@ -79,10 +89,25 @@ int enqueue_search(const nq_prefix *d_prefixes, uint64_t n, int expect_n, int mi
     Plan p;
     int rc = make_plan(max_n, min_d, diag, constrained, cfg, &p);
     if (rc) return rc;
-    unsigned long long *cursor = nullptr;
-    if (cudaMallocAsync(reinterpret_cast<void **>(&cursor), sizeof(*cursor), s) != cudaSuccess)
+    // Scratch: the work cursor, and with donation its counters and item ring.
+    const bool reg = p.layout == NQ_LAYOUT_REG || p.layout == NQ_LAYOUT_REGM;
+    // Donation (its own kernel variant, planned again: its occupancy differs)
+    // only when asked for: measured on GB300 it has not paid for its queue
+    // traffic yet, so batches short of work are better split on the host
+    // (nq_count_split).
+    const bool donate = reg && !constrained && !n_tags && cfg && cfg->donate == 2;
+    if (donate && (rc = make_plan(max_n, min_d, diag, constrained, cfg, &p, true))) return rc;
+    const size_t head_bytes = 128 + sizeof(DonateCtl);  // cursor line, counters
+    const size_t bytes = donate ? head_bytes + kDonateCap * sizeof(DonateItem) : 64;
+    unsigned char *scratch = nullptr;
+    if (cudaMallocAsync(reinterpret_cast<void **>(&scratch), bytes, s) != cudaSuccess)
         return NQ_ENOMEM;
-    rc = cuda_rc(cudaMemsetAsync(cursor, 0, sizeof(*cursor), s));
+    unsigned long long *cursor = reinterpret_cast<unsigned long long *>(scratch);
+    rc = cuda_rc(cudaMemsetAsync(scratch, 0, donate ? bytes : 64, s));
+    if (!rc && donate && d_counts)
+        rc = cuda_rc(cudaMemsetAsync(d_counts, 0, n * sizeof(uint64_t), s));
+    if (!rc && donate && d_nodes)
+        rc = cuda_rc(cudaMemsetAsync(d_nodes, 0, n * sizeof(uint64_t), s));
     if (!rc) {
         SearchArgs a{};
         a.pre = d_prefixes;
@@ -97,6 +122,12 @@ int enqueue_search(const nq_prefix *d_prefixes, uint64_t n, int expect_n, int mi
         // claim order: last index first unless index order is asked for
         a.order = (cfg && cfg->order == 1) ? 0 : 1;
         a.claim = (cfg && cfg->claim > 0) ? cfg->claim : 1;
+        a.by_tag = n_tags ? 1 : 0;
+        a.n_tags = n_tags;
+        if (donate) {
+            a.dq = reinterpret_cast<DonateCtl *>(scratch + 128);
+            a.items = reinterpret_cast<DonateItem *>(scratch + head_bytes);
+        }
         if (allowed) std::memcpy(a.allowed, allowed, sizeof(a.allowed));
         a.mul[0] = 1u;
         a.mul[1] = 2u;
@@ -104,7 +135,7 @@ int enqueue_search(const nq_prefix *d_prefixes, uint64_t n, int expect_n, int mi
         a.mul[3] = 0x80000000u;
         rc = launch_search(a, p, diag, constrained, s);
     }
-    cudaFreeAsync(cursor, s);
+    cudaFreeAsync(scratch, s);
     if (used) *used = p;
     return rc;
 }
@@ -230,6 +261,113 @@ extern "C" int nq_total_ex(int N, const nq_config *cfg, uint64_t *total_out, uin
 
 extern "C" int nq_total(int N, uint64_t *total_out) {
     return nq_total_ex(N, nullptr, total_out, nullptr, nullptr);
+}
+
+// ---------------------------------------------------------------------------
+// Host-side split: few heavy subproblems (fewer than the grid has lanes) are
+// extended a few rows deeper on the host, every child carrying its parent's
+// index in the tag field, and the kernel adds each child's count into its
+// parent's entry. The subtree of a prefix is the disjoint union of its
+// children's subtrees (Section 1), so the per-parent sums are exact.
+// ---------------------------------------------------------------------------
+extern "C" int nq_count_split(const nq_prefix *h_prefixes, uint64_t n, int rows,
+                              const nq_config *cfg, uint64_t *h_counts, uint64_t *h_nodes,
+                              uint64_t *h_totals, int *rows_used, nq_timing *timing) {
+    const auto t_start = Clock::now();
+    if (!h_counts || (n && !h_prefixes) || rows < -1 || rows > NQ_MAX_N || n > kMaxSplitParents)
+        return NQ_EINVAL;
+    if (h_totals) std::memset(h_totals, 0, 32 * sizeof(uint64_t));
+    if (n == 0) {
+        if (rows_used) *rows_used = 0;
+        return NQ_OK;
+    }
+    int min_d = NQ_MAX_N, max_n = 0;
+    for (uint64_t i = 0; i < n; ++i) {
+        min_d = std::min(min_d, (int)NQ_META_D(h_prefixes[i].meta));
+        max_n = std::max(max_n, (int)NQ_META_N(h_prefixes[i].meta));
+    }
+    if (max_n < 1 || max_n > NQ_MAX_N) return NQ_EINVAL;
+    const bool diag = h_nodes != nullptr;
+    int r = rows, rc;
+    uint64_t m = 0;
+    if (r < 0) {
+        // the fewest rows giving at least 32 children per resident lane
+        Plan p{};
+        if ((rc = make_plan(max_n, min_d, diag, false, cfg, &p))) return rc;
+        const uint64_t want = 32ull * (uint64_t)p.grid * (uint64_t)p.block;
+        for (r = 0; r < max_n - min_d; ++r) {
+            if ((rc = split_prefixes(h_prefixes, n, r, nullptr, nullptr, &m))) return rc;
+            if (m >= want) break;
+        }
+    }
+    std::vector<nq_prefix> kids;
+    std::vector<uint64_t> extra;
+    if ((rc = split_prefixes(h_prefixes, n, r, &kids, &extra, &m))) return rc;
+    const double split_ms = ms_since(t_start);
+    int kid_min_d = NQ_MAX_N;
+    for (uint64_t i = 0; i < n; ++i)
+        kid_min_d = std::min(kid_min_d, std::min((int)NQ_META_N(h_prefixes[i].meta),
+                                                 (int)NQ_META_D(h_prefixes[i].meta) + r));
+
+    CallCtx ctx;
+    if ((rc = ctx.init())) return rc;
+    nq_prefix *d_kids = nullptr;
+    uint64_t *d_counts = nullptr, *d_nodes = nullptr, *d_tot = nullptr;
+    if ((rc = ctx.alloc(&d_kids, m * sizeof(nq_prefix)))) return rc;
+    if ((rc = ctx.alloc(&d_counts, n * sizeof(uint64_t)))) return rc;
+    if (diag && (rc = ctx.alloc(&d_nodes, n * sizeof(uint64_t)))) return rc;
+    if ((rc = ctx.alloc(&d_tot, 32 * sizeof(uint64_t)))) return rc;
+    cudaEvent_t ev[3];
+    for (auto &e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) return NQ_ECUDA;
+    struct EvGuard {
+        cudaEvent_t *e;
+        ~EvGuard() {
+            for (int i = 0; i < 3; ++i) cudaEventDestroy(e[i]);
+        }
+    } evg{ev};
+    cudaEventRecord(ev[0], ctx.s);
+    rc = m ? cuda_rc(cudaMemcpyAsync(d_kids, kids.data(), m * sizeof(nq_prefix),
+                                     cudaMemcpyHostToDevice, ctx.s))
+           : NQ_OK;
+    if (!rc) rc = cuda_rc(cudaMemsetAsync(d_tot, 0, 32 * sizeof(uint64_t), ctx.s));
+    cudaEventRecord(ev[1], ctx.s);
+    Plan p{};
+    if (!rc)
+        rc = enqueue_search(d_kids, m, 0, kid_min_d, max_n, d_counts, d_nodes, d_tot, cfg,
+                            nullptr, ctx.s, &p, n);
+    cudaEventRecord(ev[2], ctx.s);
+    if (!rc)
+        rc = cuda_rc(cudaMemcpyAsync(h_counts, d_counts, n * sizeof(uint64_t),
+                                     cudaMemcpyDeviceToHost, ctx.s));
+    if (!rc && diag)
+        rc = cuda_rc(cudaMemcpyAsync(h_nodes, d_nodes, n * sizeof(uint64_t),
+                                     cudaMemcpyDeviceToHost, ctx.s));
+    if (!rc && h_totals)
+        rc = cuda_rc(cudaMemcpyAsync(h_totals, d_tot, 32 * sizeof(uint64_t),
+                                     cudaMemcpyDeviceToHost, ctx.s));
+    if (cudaStreamSynchronize(ctx.s) != cudaSuccess) return NQ_ECUDA;
+    if (rc) return rc;
+    const int st = take_device_status();
+    if (st) return st;
+    if (diag)
+        for (uint64_t i = 0; i < n; ++i) h_nodes[i] += extra[i];
+    if (rows_used) *rows_used = r;
+    if (timing) {
+        float up = 0, kern = 0;
+        cudaEventElapsedTime(&up, ev[0], ev[1]);
+        cudaEventElapsedTime(&kern, ev[1], ev[2]);
+        timing->enumerate_ms = split_ms;
+        timing->upload_ms = up;
+        timing->kernel_ms = kern;
+        timing->prefixes = m;
+        timing->d = kid_min_d;
+        timing->layout = p.layout;
+        timing->block = p.block;
+        timing->grid = p.grid;
+        timing->total_ms = ms_since(t_start);
+    }
+    return NQ_OK;
 }
 
 // ---------------------------------------------------------------------------

@@ -10,6 +10,29 @@
 
 namespace nqi {
 
+// Subtree donation (register layouts): counters and a ring of donated
+// frames in per-launch scratch memory, zeroed before the launch.
+// Ticket scheme: a lane with nothing to do takes ticket t (tail) and waits for
+// item t; donors publish items in order (head). Each counter has its own
+// 128-byte line.
+struct DonateCtl {
+    unsigned long long head;     // items published
+    unsigned long long pad0[15];
+    unsigned long long tail;     // tickets issued
+    unsigned long long pad1[15];
+    unsigned long long served;   // tickets whose item was read
+    unsigned long long pad2[15];
+    unsigned long long started;  // lanes that have entered the kernel
+    int error;
+    int pad3[29];
+};
+// A donated frame {cols, ld, rd, avail} and {origin lo, origin hi, weight|N<<2, seq}.
+struct DonateItem {
+    uint4 frame;
+    uint4 info;
+};
+constexpr unsigned kDonateCap = 4096;  // ring entries (power of two)
+
 // Arguments of one search launch (device pointers unless noted).
 struct SearchArgs {
     const nq_prefix *pre;          // [n] subproblems
@@ -26,6 +49,12 @@ struct SearchArgs {
     // Constrained mode only (partial-board queries): the columns each row may
     // take; rows >= N and entry 31 must be 0.
     uint32_t allowed[32];
+    // Split subproblems: counts/nodes of record i are added to entry
+    // tag(i) = meta >> 12, which must be below n_tags (else NQ_EINVAL).
+    int by_tag;
+    uint64_t n_tags;
+    DonateCtl *dq;                   // donation counters (NULL: no donation)
+    DonateItem *items;               // [kDonateCap]
     // Multipliers 1, 2, 2^32-1 and 2^31 for the multiply-add form of the step
     // (layout WTM). Passed at run time so that the compiler cannot fold them:
     // the products must be issued as integer multiply-adds on the FMA pipe.
@@ -92,6 +121,7 @@ struct Plan {
     int slots;      // frames per thread
     size_t smem;    // dynamic shared memory per block, bytes
     int sms;        // multiprocessors of the device
+    bool donate;    // the kernel variant with subtree donation
 };
 
 // Stack slots a layout needs for prefixes of depth >= min_d on boards <= max_n
@@ -99,7 +129,8 @@ struct Plan {
 int slots_needed(int layout, int max_n, int min_d);
 
 // Resolve cfg (may be NULL) into a launch shape for the current device.
-int make_plan(int max_n, int min_d, bool diag, bool constrained, const nq_config *cfg, Plan *plan);
+int make_plan(int max_n, int min_d, bool diag, bool constrained, const nq_config *cfg, Plan *plan,
+              bool donate = false);
 
 // Enqueue the search kernel. Returns NQ_OK or NQ_ECUDA.
 int launch_search(const SearchArgs &a, const Plan &p, bool diag, bool constrained, cudaStream_t s);
@@ -109,6 +140,15 @@ int take_device_status();
 
 // Host enumeration helpers (prefix.cpp).
 uint32_t meta_of(int weight, int n, int d);
+
+// Expand each subproblem `rows` rows deeper (all placements, the parent's
+// weight; the tag field names the parent). n_children = number of children;
+// extra_nodes[i] (optional) = placements made on the way below parent i;
+// out == nullptr: count only.
+constexpr uint64_t kMaxSplitParents = 1ull << 20;    // the 20-bit tag field
+constexpr uint64_t kMaxSplitChildren = 1ull << 27;   // 2 GiB of records
+int split_prefixes(const nq_prefix *in, uint64_t n, int rows, std::vector<nq_prefix> *out,
+                   std::vector<uint64_t> *extra_nodes, uint64_t *n_children);
 
 // Partial-board constraints (constrain.cpp): per-row allowed masks (rows >= N
 // zero) and whether the listed queens conflict; the prefix rows under them.

@@ -139,22 +139,6 @@ unsigned worker_count() {
     return h ? std::min(h, 64u) : 1u;
 }
 
-}  // namespace
-}  // namespace nqi
-
-using namespace nqi;
-
-// Depth 7 gives 2M (N=16) to 61M (N=22) subproblems: enough for every lane of
-// a full GB300 grid to claim tens of them (measured best or within 3% from
-// N=16 to N=22). Beyond N=22 depth 7 would exceed ~10^8 records, so 6.
-extern "C" int nq_default_depth(int N) {
-    if (N < 1 || N > NQ_MAX_N) return NQ_EINVAL;
-    const int d = N <= 22 ? 7 : 6;
-    return std::max(0, std::min(d, N - 2));
-}
-
-namespace {
-
 // Run fn(i) for i in [0, n) on the host's cores, pulling indices dynamically.
 template <typename F>
 void parallel_for(size_t n, F fn) {
@@ -173,7 +157,21 @@ void parallel_for(size_t n, F fn) {
     for (auto &x : th) x.join();
 }
 
+
 }  // namespace
+}  // namespace nqi
+
+using namespace nqi;
+
+// Depth 7 gives 2M (N=16) to 61M (N=22) subproblems: enough for every lane of
+// a full GB300 grid to claim tens of them (measured best or within 3% from
+// N=16 to N=22). Beyond N=22 depth 7 would exceed ~10^8 records, so 6.
+extern "C" int nq_default_depth(int N) {
+    if (N < 1 || N > NQ_MAX_N) return NQ_EINVAL;
+    const int d = N <= 22 ? 7 : 6;
+    return std::max(0, std::min(d, N - 2));
+}
+
 
 extern "C" int nq_enumerate_prefixes(int N, int d, nq_prefix *out, uint64_t cap, uint64_t *n_out) {
     if (N < 1 || N > NQ_MAX_N || d < 0 || d > N || !n_out) return NQ_EINVAL;
@@ -206,6 +204,69 @@ extern "C" int nq_enumerate_prefixes(int N, int d, nq_prefix *out, uint64_t cap,
     });
     return total > cap ? NQ_EOVERFLOW : NQ_OK;
 }
+
+namespace nqi {
+
+
+namespace {
+// All extensions of one state by the rows up to `target` (no symmetry rule):
+// emits children (when out != NULL) and counts the placements on the way.
+void expand_rec(int n, int target, int row, uint32_t cols, uint32_t ld, uint32_t rd,
+                uint32_t meta_hi, nq_prefix *out, uint64_t &cnt, uint64_t &nodes) {
+    const uint32_t last = mask_n(n);
+    if (row == target) {
+        if (out) out[cnt] = nq_prefix{cols, ld & last, rd, meta_hi | ((uint32_t)target << 7)};
+        ++cnt;
+        return;
+    }
+    uint32_t av = last & ~(cols | ld | rd);
+    while (av) {
+        const uint32_t p = low_bit(av);
+        av ^= p;
+        ++nodes;
+        expand_rec(n, target, row + 1, cols | p, ((ld | p) << 1) & last, (rd | p) >> 1, meta_hi,
+                   out, cnt, nodes);
+    }
+}
+}  // namespace
+
+int split_prefixes(const nq_prefix *in, uint64_t n, int rows, std::vector<nq_prefix> *out,
+                   std::vector<uint64_t> *extra_nodes, uint64_t *n_children) {
+    if (n > kMaxSplitParents || rows < 0 || (n && !in)) return NQ_EINVAL;
+    for (uint64_t i = 0; i < n; ++i) {
+        const int N = (int)NQ_META_N(in[i].meta), d = (int)NQ_META_D(in[i].meta);
+        const int w = (int)NQ_META_WEIGHT(in[i].meta);
+        if (N < 1 || d > N || (w != 1 && w != 2) || (in[i].cols & ~mask_n(N)) ||
+            __builtin_popcount(in[i].cols) != d)
+            return NQ_EINVAL;
+    }
+    auto run = [&](uint64_t i, nq_prefix *dst, uint64_t &cnt, uint64_t &nodes) {
+        const int N = (int)NQ_META_N(in[i].meta), d = (int)NQ_META_D(in[i].meta);
+        const uint32_t hi = NQ_META_WEIGHT(in[i].meta) | ((uint32_t)N << 2) | ((uint32_t)i << 12);
+        expand_rec(N, std::min(N, d + rows), d, in[i].cols, in[i].ld & mask_n(N),
+                   in[i].rd & mask_n(N), hi, dst, cnt, nodes);
+    };
+    std::vector<uint64_t> first(n + 1, 0), extra(n, 0);
+    parallel_for(n, [&](size_t i) {
+        uint64_t cnt = 0, nodes = 0;
+        run(i, nullptr, cnt, nodes);
+        first[i + 1] = cnt;
+        extra[i] = nodes;
+    });
+    for (uint64_t i = 0; i < n; ++i) first[i + 1] += first[i];
+    *n_children = first[n];
+    if (extra_nodes) extra_nodes->swap(extra);
+    if (!out) return NQ_OK;
+    if (first[n] > kMaxSplitChildren) return NQ_EOVERFLOW;
+    out->resize(first[n]);
+    parallel_for(n, [&](size_t i) {
+        uint64_t cnt = 0, nodes = 0;
+        run(i, out->data() + first[i], cnt, nodes);
+    });
+    return NQ_OK;
+}
+
+}  // namespace nqi
 
 extern "C" int nq_descendants(const nq_prefix *parent, int rows, nq_prefix *out, uint64_t cap,
                               uint64_t *n_out) {

@@ -82,6 +82,35 @@ __device__ __forceinline__ void sts1(uint32_t a, uint32_t v) {
     asm volatile("st.shared.u32 [%0], %1;" : : "r"(a), "r"(v) : "memory");
 }
 
+__device__ __forceinline__ uint4 ldcg4(const void *p) {
+    uint4 v;
+    asm volatile("ld.global.cg.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p)
+                 : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned long long ldcg8(const void *p) {
+    unsigned long long v;
+    asm volatile("ld.global.cg.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned int ldcg4b(const void *p) {
+    unsigned int v;
+    asm volatile("ld.global.cg.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void stcg4(void *p, uint4 v) {
+    asm volatile("st.global.cg.v4.u32 [%0], {%1, %2, %3, %4};"
+                 :
+                 : "l"(p), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w)
+                 : "memory");
+}
+
+constexpr unsigned kReadySpins = 1u << 20;   // wait for a reserved item to be written
+constexpr int kMinDonateRows = 11;  // donate only frames with >= 11 rows below (~1e4+ nodes)
+constexpr unsigned kMaxIdleRounds = 1u << 21;  // polls (<= 64 us apart): gives up after ~2 min
+
 // True when the child state c2 has exactly one free column left (bits >= N
 // are pre-set), i.e. queens now sit in rows 0..N-2: Algorithm 3's
 // popc(cur) == N-1 test, which with the pre-set high bits reads popc == 31.
@@ -384,8 +413,8 @@ __device__ __forceinline__ void step_paper(uint32_t &top, const Lane &k, uint32_
     }
 }
 
-template <int LAYOUT, bool DIAG, bool CONSTR>
-__global__ void __maxnreg__(48) search_kernel(const SearchArgs a) {
+template <int LAYOUT, bool DIAG, bool CONSTR, bool DONATE>
+__device__ __forceinline__ void search_body(const SearchArgs &a) {
     constexpr bool kRegm = LAYOUT == NQ_LAYOUT_REGM;
     constexpr bool kReg = LAYOUT == NQ_LAYOUT_REG || kRegm;
     constexpr bool kWt = LAYOUT == NQ_LAYOUT_WT;
@@ -439,9 +468,40 @@ __global__ void __maxnreg__(48) search_kernel(const SearchArgs a) {
     uint64_t next_i = 0;  // claimed, not yet started: next_i .. next_i + rem - 1
     uint32_t rem = 0;
 
+    // With donation a subproblem's count can arrive in several parts (the
+    // host zeroes counts and nodes first), so the parts are added.
+    constexpr bool donating = DONATE && kReg && !CONSTR;
+    uint32_t waits = 0;
+    uint64_t ticket = kNone;    // donation ticket this lane waits on
+    // lane 0: the donation counters as loaded at the last bookkeeping point
+    unsigned long long pf_head = 0, pf_tail = 0;
+    // Lanes count themselves in on entry: a block that starts late (another
+    // kernel holding its SM) finds the queue empty and leaves by itself, so the
+    // exit test never waits for blocks that have not started.
+    if (donating && lane == 0) atomicAdd(&a.dq->started, 32ull);
     auto finish = [&](uint64_t i, uint64_t s, uint64_t nodes_below, uint32_t w, uint32_t n) {
-        if (a.counts) a.counts[i] = s;
-        if (DIAG && a.nodes) a.nodes[i] = nodes_below;
+        if (a.by_tag) {
+            // split subproblems: the count goes to the parent named by the tag
+            const uint64_t parent = __ldg(reinterpret_cast<const uint32_t *>(a.pre + i) + 3) >> 12;
+            if (parent >= a.n_tags) {
+                record_error(NQ_EINVAL);
+            } else if (a.counts && s)
+                atomicAdd(reinterpret_cast<unsigned long long *>(&a.counts[parent]),
+                          (unsigned long long)s);
+            if (DIAG && a.nodes && nodes_below && parent < a.n_tags)
+                atomicAdd(reinterpret_cast<unsigned long long *>(&a.nodes[parent]),
+                          (unsigned long long)nodes_below);
+        } else if (donating) {
+            if (a.counts && s)
+                atomicAdd(reinterpret_cast<unsigned long long *>(&a.counts[i]),
+                          (unsigned long long)s);
+            if (DIAG && a.nodes && nodes_below)
+                atomicAdd(reinterpret_cast<unsigned long long *>(&a.nodes[i]),
+                          (unsigned long long)nodes_below);
+        } else {
+            if (a.counts) a.counts[i] = s;
+            if (DIAG && a.nodes) a.nodes[i] = nodes_below;
+        }
         if (a.totals && s) {
             if (n != wsum_n && wsum != 0) {
                 atomicAdd(reinterpret_cast<unsigned long long *>(&a.totals[wsum_n]),
@@ -557,7 +617,168 @@ __global__ void __maxnreg__(48) search_kernel(const SearchArgs a) {
             }
             need_mask = __ballot_sync(~0u, need);
         }
-        if (__all_sync(~0u, exhausted && idx == kNone)) break;
+        if (donating) {
+            // ---- subtree donation, once the main queue is exhausted ----------
+            // A lane with nothing left takes a ticket and polls only its own
+            // ring slot; busy lanes hand shallow frames to outstanding tickets.
+            DonateCtl *q = a.dq;
+            const bool free_lane = top == idle_top && exhausted && idx == kNone;
+            {  // new waiters: one ticket range per warp
+                const bool want = free_lane && ticket == kNone;
+                const unsigned wmask = __ballot_sync(~0u, want);
+                if (wmask) {
+                    const int leader = __ffs(wmask) - 1;
+                    unsigned long long first = 0;
+                    if ((int)lane == leader)
+                        first = atomicAdd(&q->tail, (unsigned long long)__popc(wmask));
+                    first = __shfl_sync(~0u, first, leader);
+                    if (want) ticket = first + __popc(wmask & lt_mask);
+                }
+            }
+            // (1) waiters whose item has been written take it
+            bool took = false;
+            if (ticket != kNone) {
+                const uint32_t s0 = (uint32_t)(ticket & (kDonateCap - 1));
+                DonateItem *it = a.items + s0;
+                const uint4 info = ldcg4(&it->info);
+                if (info.w == (uint32_t)(ticket + 1) - s0) {
+                    __threadfence();
+                    const uint4 f = ldcg4(&it->frame);
+                    __threadfence();
+                    // free the slot for item ticket + cap
+                    stcg4(&it->info, make_uint4(info.x, info.y, info.z,
+                                                (uint32_t)(ticket + kDonateCap) - s0));
+                    idx = (uint64_t)info.x | ((uint64_t)info.y << 32);
+                    wt = info.z & 3u;
+                    pn = (info.z >> 2) & 31u;
+                    sol = 0;
+                    nod = 0;
+                    c = f.x; l = f.y; r = f.z; av = f.w;
+                    top = k.base + k.stride;
+                    ticket = kNone;
+                    took = true;
+                }
+            }
+            {
+                const unsigned tk = __ballot_sync(~0u, took);
+                if (tk && (int)lane == __ffs(tk) - 1)
+                    atomicAdd(&q->served, (unsigned long long)__popc(tk));
+            }
+            // (2) busy lanes split off shallow frames while tickets wait. The
+            // counters come from lane 0's loads at the previous bookkeeping
+            // point, so their latency hides behind the search steps.
+            const unsigned long long snap_h = __shfl_sync(~0u, pf_head, 0);
+            const unsigned long long snap_t = __shfl_sync(~0u, pf_tail, 0);
+            if (lane == 0) {
+                pf_head = ldcg8(&q->head);
+                pf_tail = ldcg8(&q->tail);
+            }
+            if (snap_t > snap_h) {
+                // Only frames with at least kMinDonateRows rows below them are
+                // worth a trip through the queue; the row of a frame is
+                // popc(cols) - (32 - N) with the columns >= N pre-set.
+                uint32_t dslot = 0;
+                uint4 df = make_uint4(0, 0, 0, 0);
+                if (idx != kNone && top != idle_top) {
+                    const int row_limit = 32 - kMinDonateRows;
+                    for (uint32_t sl = k.base + k.stride; sl < top; sl += k.stride) {
+                        const uint4 f = lds4(sl);
+                        if (__popc(f.x) > row_limit) break;  // deeper frames follow
+                        if (__popc(f.w) >= 2) {
+                            dslot = sl;
+                            df = f;
+                            break;
+                        }
+                    }
+                    if (!dslot && __popc(c) <= row_limit && __popc(av) >= 2)
+                        df = make_uint4(c, l, r, av);
+                }
+                const bool can = df.w != 0u;
+                const unsigned dmask = __ballot_sync(~0u, can);
+                if (dmask) {
+                    // Publish no more items than there are tickets: head never
+                    // passes tail, so every item has a lane waiting for it and a
+                    // slot is only ever reused after an issued ticket's read.
+                    const int leader = __ffs(dmask) - 1;
+                    unsigned long long first = 0, got = 0;
+                    if ((int)lane == leader) {
+                        unsigned long long h = ldcg8(&q->head);
+                        for (int it = 0; it < 32; ++it) {
+                            const unsigned long long t = ldcg8(&q->tail);
+                            unsigned long long k2 = t > h ? t - h : 0ull;
+                            if (k2 > (unsigned long long)__popc(dmask)) k2 = __popc(dmask);
+                            if (k2 == 0) break;
+                            const unsigned long long old = atomicCAS(&q->head, h, h + k2);
+                            if (old == h) {
+                                first = h;
+                                got = k2;
+                                break;
+                            }
+                            h = old;
+                        }
+                    }
+                    first = __shfl_sync(~0u, first, leader);
+                    got = __shfl_sync(~0u, got, leader);
+                    const unsigned rank = __popc(dmask & lt_mask);
+                    if (can && rank < got) {
+                        const unsigned long long j = first + rank;
+                        const uint32_t s0 = (uint32_t)(j & (kDonateCap - 1));
+                        DonateItem *it = a.items + s0;
+                        // wait until the slot's previous item has been read
+                        unsigned spins = 0;
+                        while (ldcg4b(&it->info.w) != (uint32_t)j - s0 && ++spins < kReadySpins)
+                            __nanosleep(128);
+                        if (spins >= kReadySpins) {
+                            record_error(NQ_ETIMEOUT);
+                        } else {
+                            const uint32_t keep = df.w & (0u - df.w);
+                            const uint32_t give = df.w ^ keep;
+                            if (dslot) sts1(dslot + 12u, keep);
+                            else av = keep;
+                            stcg4(&it->frame, make_uint4(df.x, df.y, df.z, give));
+                            __threadfence();
+                            stcg4(&it->info, make_uint4((uint32_t)idx, (uint32_t)(idx >> 32),
+                                                        wt | (pn << 2), (uint32_t)(j + 1) - s0));
+                        }
+                    }
+                }
+            }
+            // (3) a warp of waiters leaves once no lane is busy and every
+            // published item has been read (head read before and after the
+            // other counters, so the snapshot is consistent)
+            if (__all_sync(~0u, ticket != kNone)) {
+                int done = 0;
+                if (lane == 0) {
+                    ++waits;
+                    if ((waits & 15u) == 0u) {
+                        const unsigned long long h1 = ldcg8(&q->head);
+                        __threadfence();
+                        const unsigned long long st = ldcg8(&q->started);
+                        const unsigned long long tl = ldcg8(&q->tail);
+                        const unsigned long long sv = ldcg8(&q->served);
+                        __threadfence();
+                        const unsigned long long h2 = ldcg8(&q->head);
+                        done = (h1 == h2 && st + sv == tl && h1 == sv) ? 1 : 0;
+                    }
+                    if (!done && waits > kMaxIdleRounds) {
+                        atomicExch(&q->error, NQ_ETIMEOUT);
+                        done = 2;
+                    }
+                }
+                done = __shfl_sync(~0u, done, 0);
+                if (done) {
+                    if (done == 2) record_error(NQ_ETIMEOUT);
+                    break;
+                }
+                // back-off: 0.5 us doubling to 64 us while nothing comes
+                const uint32_t w = __shfl_sync(~0u, waits, 0);
+                __nanosleep(512u << (w < 112u ? w >> 4 : 7u));
+                continue;
+            }
+            waits = 0;
+        } else if (__all_sync(~0u, exhausted && idx == kNone)) {
+            break;
+        }
 
         uint32_t s32 = 0, n32 = 0;
 #pragma unroll
@@ -775,15 +996,35 @@ __global__ void __maxnreg__(64) serve_kernel(const ServeArgs a) {
     }
 }
 
+// The production kernel is held to 48 registers (5 resident blocks of 256 at
+// N=18, d=7); the donating variant carries the queue logic and gets 64.
 template <int LAYOUT, bool DIAG, bool CONSTR>
-void *kernel_ptr() {
-    return reinterpret_cast<void *>(&search_kernel<LAYOUT, DIAG, CONSTR>);
+__global__ void __maxnreg__(48) search_kernel(const SearchArgs a) {
+    search_body<LAYOUT, DIAG, CONSTR, false>(a);
+}
+template <int LAYOUT, bool DIAG>
+__global__ void __maxnreg__(64) search_kernel_donate(const SearchArgs a) {
+    search_body<LAYOUT, DIAG, false, true>(a);
 }
 
-void *pick_kernel(int layout, bool diag, bool constrained) {
+template <int LAYOUT, bool DIAG, bool CONSTR, bool DONATE = false>
+void *kernel_ptr() {
+    if constexpr (DONATE)
+        return reinterpret_cast<void *>(&search_kernel_donate<LAYOUT, DIAG>);
+    else
+        return reinterpret_cast<void *>(&search_kernel<LAYOUT, DIAG, CONSTR>);
+}
+
+void *pick_kernel(int layout, bool diag, bool constrained, bool donate = false) {
     if (constrained)
         return diag ? kernel_ptr<NQ_LAYOUT_REG, true, true>()
                     : kernel_ptr<NQ_LAYOUT_REG, false, true>();
+    if (donate && layout == NQ_LAYOUT_REGM)
+        return diag ? kernel_ptr<NQ_LAYOUT_REGM, true, false, true>()
+                    : kernel_ptr<NQ_LAYOUT_REGM, false, false, true>();
+    if (donate && layout == NQ_LAYOUT_REG)
+        return diag ? kernel_ptr<NQ_LAYOUT_REG, true, false, true>()
+                    : kernel_ptr<NQ_LAYOUT_REG, false, false, true>();
     if (layout == NQ_LAYOUT_PAPER)
         return diag ? kernel_ptr<NQ_LAYOUT_PAPER, true, false>()
                     : kernel_ptr<NQ_LAYOUT_PAPER, false, false>();
@@ -815,7 +1056,7 @@ int slots_needed(int layout, int max_n, int min_d) {
 }
 
 int make_plan(int max_n, int min_d, bool diag, bool constrained, const nq_config *cfg,
-              Plan *plan) {
+              Plan *plan, bool donate) {
     if (max_n < 1 || max_n > NQ_MAX_N || min_d < 0 || min_d > max_n) return NQ_EINVAL;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return NQ_ECUDA;
@@ -839,7 +1080,8 @@ int make_plan(int max_n, int min_d, bool diag, bool constrained, const nq_config
         p.block = fit;
     }
     p.smem = (size_t)p.block * per_thread + extra;
-    void *k = pick_kernel(p.layout, diag, constrained);
+    p.donate = donate && (p.layout == NQ_LAYOUT_REG || p.layout == NQ_LAYOUT_REGM) && !constrained;
+    void *k = pick_kernel(p.layout, diag, constrained, p.donate);
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem) !=
         cudaSuccess)
         return NQ_ECUDA;
@@ -857,7 +1099,7 @@ int make_plan(int max_n, int min_d, bool diag, bool constrained, const nq_config
 int launch_search(const SearchArgs &a, const Plan &p, bool diag, bool constrained,
                   cudaStream_t s) {
     if (a.n == 0) return NQ_OK;
-    void *k = pick_kernel(p.layout, diag, constrained);
+    void *k = pick_kernel(p.layout, diag, constrained, p.donate && a.dq != nullptr);
     SearchArgs args = a;
     void *params[] = {&args};
     const cudaError_t e = cudaLaunchKernel(k, dim3(p.grid), dim3(p.block), params, p.smem, s);

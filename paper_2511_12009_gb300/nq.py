@@ -38,7 +38,7 @@ class Config(ctypes.Structure):
     _fields_ = [("layout", ctypes.c_int32), ("block", ctypes.c_int32),
                 ("blocks_per_sm", ctypes.c_int32), ("order", ctypes.c_int32),
                 ("d", ctypes.c_int32), ("claim", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 2)]
+                ("donate", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class Timing(ctypes.Structure):
@@ -71,6 +71,8 @@ def _declare(lib):
         "nq_total": (_i32, [_i32, ctypes.POINTER(_u64)]),
         "nq_total_ex": (_i32, [_i32, ctypes.POINTER(Config), ctypes.POINTER(_u64),
                                ctypes.POINTER(_u64), ctypes.POINTER(Timing)]),
+        "nq_count_split": (_i32, [_vp, _u64, _i32, ctypes.POINTER(Config), _vp, _vp, _vp,
+                                  ctypes.POINTER(_i32), ctypes.POINTER(Timing)]),
         "nq_count_constrained": (_i32, [_i32, ctypes.POINTER(Queen), _i32, ctypes.POINTER(_u64)]),
         "nq_strerror": (ctypes.c_char_p, [_i32]),
         "nq_probe_alu": (_i32, [_i32, _i32, ctypes.POINTER(ctypes.c_double),
@@ -125,11 +127,11 @@ def _stream_handle(stream) -> int | None:
     return stream.cuda_stream
 
 
-def make_config(layout=0, block=0, blocks_per_sm=0, order=0, d=0, claim=0) -> Config:
+def make_config(layout=0, block=0, blocks_per_sm=0, order=0, d=0, claim=0, donate=0) -> Config:
     if isinstance(layout, str):
         layout = LAYOUTS[layout]
     return Config(int(layout), int(block), int(blocks_per_sm), int(order), int(d), int(claim),
-                  (0, 0))
+                  int(donate), 0)
 
 
 # --- host prefix generation --------------------------------------------------
@@ -229,6 +231,31 @@ def total_ex(n: int, config: Config | None = None, nodes: bool = False) -> dict:
            "d": tm.d, "layout": tm.layout, "block": tm.block, "grid": tm.grid}
     if nodes:
         res["nodes"] = int(nod.value)
+    return res
+
+
+def count_split(prefixes: np.ndarray, rows: int = -1, config: Config | None = None,
+                nodes: bool = False) -> dict:
+    """nq_count_split on host records: per-prefix counts (and nodes), per-N
+    weighted totals, the rows added and the call's timing."""
+    pre = np.ascontiguousarray(prefixes, dtype=PREFIX_DTYPE)
+    n = len(pre)
+    counts = np.zeros(max(n, 1), dtype=np.uint64)
+    nod = np.zeros(max(n, 1), dtype=np.uint64) if nodes else None
+    totals = np.zeros(32, dtype=np.uint64)
+    used = _i32(0)
+    tm = Timing()
+    cfg = ctypes.byref(config) if config is not None else None
+    _check(lib().nq_count_split(pre.ctypes.data if n else None, n, int(rows), cfg,
+                                counts.ctypes.data, nod.ctypes.data if nodes else None,
+                                totals.ctypes.data, ctypes.byref(used), ctypes.byref(tm)),
+           "nq_count_split")
+    res = {"counts": counts[:n], "totals": totals, "rows": int(used.value),
+           "children": int(tm.prefixes), "split_ms": tm.enumerate_ms, "upload_ms": tm.upload_ms,
+           "kernel_ms": tm.kernel_ms, "total_ms": tm.total_ms, "layout": tm.layout,
+           "block": tm.block, "grid": tm.grid}
+    if nodes:
+        res["nodes"] = nod[:n]
     return res
 
 

@@ -119,3 +119,24 @@ def test_default_depth_in_range():
     for n in range(1, 32):
         d = nq.default_depth(n)
         assert 0 <= d <= max(n - 2, 0)
+
+
+def test_count_split_argument_errors():
+    """Rejected on the host before any device work."""
+    pre = nq.enumerate_prefixes(10, 3).copy()
+    cnt = np.zeros(len(pre), dtype=np.uint64)
+    lib = nq.lib()
+    assert lib.nq_count_split(pre.ctypes.data, len(pre), 2, None, None, None, None, None,
+                              None) == nq.NQ_EINVAL                       # no counts
+    assert lib.nq_count_split(pre.ctypes.data, len(pre), -2, None, cnt.ctypes.data, None, None,
+                              None, None) == nq.NQ_EINVAL                 # rows < -1
+    assert lib.nq_count_split(pre.ctypes.data, (1 << 20) + 1, 2, None, cnt.ctypes.data, None,
+                              None, None, None) == nq.NQ_EINVAL           # over the tag width
+    bad = pre.copy()
+    bad["cols"][0] |= np.uint32(1 << 12)                                  # off the board
+    assert lib.nq_count_split(bad.ctypes.data, len(bad), 2, None, cnt.ctypes.data, None, None,
+                              None, None) == nq.NQ_EINVAL
+    tot = np.full(32, 7, dtype=np.uint64)
+    assert lib.nq_count_split(None, 0, 2, None, cnt.ctypes.data, None, tot.ctypes.data, None,
+                              None) == nq.NQ_OK
+    assert int(tot.sum()) == 0

@@ -227,3 +227,78 @@ def test_constrained_special_cases(orc):
 def test_total_n21_n22():
     assert nq.total(21) == Q[21]
     assert nq.total(22) == Q[22]
+
+
+@pytest.mark.parametrize("layout", ["regm", "reg"])
+@pytest.mark.parametrize("n,d", [(16, 2), (15, 1), (17, 4), (14, 0)])
+def test_subtree_donation(orc, layout, n, d):
+    """Few heavy prefixes: nearly every lane starts idle and the work spreads by
+    donation. Per-prefix counts and nodes equal the oracle's and the run with
+    donation switched off."""
+    pre = nq.enumerate_prefixes(n, d)
+    want_c, want_n = oracle_counts(orc, n, d)
+    for donate in (2, 1):
+        got_c, got_n, tot = run(pre, d, n, layout, nodes=True, donate=donate)
+        assert np.array_equal(got_c, want_c), donate
+        assert np.array_equal(got_n, want_n), donate
+        assert int(tot[n]) == Q[n]
+        got_c2, _, tot2 = run(pre, d, n, layout, donate=donate)
+        assert np.array_equal(got_c2, want_c) and int(tot2[n]) == Q[n]
+
+
+def test_nodes_at_bench_depth_equal_oracle_by_refinement():
+    """N=18 at d=7: the node total of the diagnostic kernel equals the oracle's
+    d=5 node total minus the placements of rows 5 and 6 (the d=6 and d=7 prefix
+    counts), so the bench's node count is pinned by the oracle."""
+    g = np.load(os.path.join(GOLDEN, "oracle_n18_d5.npz"))
+    r = nq.total_ex(18, nq.make_config(d=7), nodes=True)
+    assert r["total"] == Q[18]
+    assert r["nodes"] == int(g["nodes"].sum()) - nq.prefix_count(18, 6) - nq.prefix_count(18, 7)
+
+
+@pytest.mark.parametrize("layout", ["regm", "reg", "wt"])
+@pytest.mark.parametrize("n,d,rows", [(16, 2, 3), (15, 1, 4), (13, 4, -1), (12, 0, 5),
+                                      (10, 6, 9), (9, 9, 2)])
+def test_host_split_equals_oracle(orc, layout, n, d, rows):
+    """nq_count_split: each prefix is expanded `rows` rows on the host and the
+    children's counts and nodes are added into the parent's entry. Per-prefix
+    counts and nodes equal the oracle's; rows past the last row are capped
+    (d = N: the prefixes are solutions)."""
+    pre = nq.enumerate_prefixes(n, d)
+    want_c, want_n = oracle_counts(orc, n, d)
+    r = nq.count_split(pre, rows, nq.make_config(layout), nodes=True)
+    assert np.array_equal(r["counts"], want_c)
+    assert np.array_equal(r["nodes"], want_n)
+    assert int(r["totals"][n]) == Q[n]
+    r2 = nq.count_split(pre, rows, nq.make_config(layout))
+    assert np.array_equal(r2["counts"], want_c) and int(r2["totals"][n]) == Q[n]
+    if rows >= 0:
+        assert r["rows"] == rows
+
+
+def test_host_split_golden_and_mixed(orc):
+    """N=16 at d=5 against the stored oracle counts and nodes (auto rows), and
+    N=10..14 mixed and shuffled in one split call."""
+    g = np.load(os.path.join(GOLDEN, "oracle_n16_d5.npz"))
+    r = nq.count_split(nq.enumerate_prefixes(16, 5), -1, nodes=True)
+    assert np.array_equal(r["counts"], g["counts"]) and np.array_equal(r["nodes"], g["nodes"])
+    assert int(r["totals"][16]) == Q[16]
+    parts, want = [], []
+    for n in range(10, 15):
+        parts.append(nq.enumerate_prefixes(n, 2))
+        want.append(oracle_counts(orc, n, 2)[0])
+    pre = np.concatenate(parts)
+    perm = np.random.default_rng(11).permutation(len(pre))
+    r = nq.count_split(pre[perm], 3)
+    assert np.array_equal(r["counts"], np.concatenate(want)[perm])
+    for n in range(10, 15):
+        assert int(r["totals"][n]) == Q[n]
+
+
+def test_host_split_rejects_bad_input():
+    pre = nq.enumerate_prefixes(10, 3).copy()
+    pre["meta"][4] = (pre["meta"][4] & ~np.uint32(3)) | np.uint32(3)    # weight 3
+    with pytest.raises(nq.NQError):
+        nq.count_split(pre, 2)
+    r = nq.count_split(pre[:0], 2)
+    assert len(r["counts"]) == 0 and int(r["totals"].sum()) == 0

@@ -6,7 +6,8 @@ depth-10 descendants (index = draw mod count; a prefix with none is skipped
 and the next rank taken). Depth 10 keeps each subtree near a few CPU-core
 seconds of oracle work. The GPU counts all 4096; the oracle, with its own
 unranking and its own descendant enumeration, re-derives the first 256
-prefixes and counts them one by one. Exact equality throughout.
+prefixes and counts them one by one; the host-split call must give the
+same 4096 counts. Exact equality throughout.
 """
 import numpy as np
 import pytest
@@ -69,3 +70,7 @@ def test_probe_counts_against_oracle(orc, sample):
         assert (int(rec["cols"]), int(rec["ld"]), int(rec["rd"])) == to_state(N, cl)
     want, _ = orc.count_prefixes(N, np.array(oracle_cols, dtype=np.int8))
     assert np.array_equal(got[:CHECK], want)
+    # the host split (children searched in one launch, summed per parent) agrees
+    split = nq.count_split(pre, -1)
+    assert split["rows"] >= 1
+    assert np.array_equal(split["counts"], got)
