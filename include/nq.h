@@ -383,6 +383,61 @@ int nq_count_host_noalloc(int N, int d, const nq_prefix *h_prefixes, uint64_t n,
  */
 int nq_probe_alu(int kind, int iters, double *per_clk_per_sm, double *per_s, double *sm_mhz);
 
+/*
+ * Shared-memory access pattern probe, for reading a profiler's bank-conflict
+ * and wavefront counters on a known pattern (Section 3.1's claim of
+ * conflict-free stack accesses, checked on this GPU). One launch of SMs x
+ * resident blocks x 256 threads, `slots` (1..16) stack slots per thread; each
+ * of iters x 8 iterations, every lane whose bit is set in lane_mask (and, for
+ * density < 32, whose pseudo-random draw is below density/32) makes one
+ * access to a pseudo-random slot of its own stack:
+ *   kind 0  16-byte load of a frame, frames interleaved by thread (the search
+ *           kernel's layout, nq_stack_offset)
+ *   kind 1  16-byte store, same addresses
+ *   kind 2  4-byte load, 32-bit words interleaved by thread (WT32)
+ *   kind 3  16-byte load, each thread's frames contiguous (slot k of thread t
+ *           at (t x slots + k) x 16): a per-thread stack, the counter-example
+ * ms_out = CUDA-event time of the launch. Synchronous; allocates and frees its
+ * own output buffer.
+ */
+int nq_probe_smem(int kind, uint32_t lane_mask, int density, int iters, int slots,
+                  double *ms_out);
+
+/*
+ * Byte offset, within a block's dynamic shared memory, of 32-bit field `field`
+ * (0 cols, 1 ld, 2 rd, 3 avail) of stack slot `slot` (0 = the sentinel) of
+ * thread `thread`, for a block of `block` threads with `slots` slots per
+ * thread, in layout `layout` -- the addresses the search kernel computes (the
+ * kernel and this call share one definition). Whole-frame layouts (PAPER, REG,
+ * REGM, WT, WTM) put slot k of thread t at (k x block + t) x 16 and move
+ * frames as 16-byte accesses; WT and WTM also store the avail word alone
+ * (4 bytes). WT32 / WT32A keep four arrays of 32-bit words, word k of thread
+ * t at (k x block + t) x 4 in each, and make only 4-byte accesses. A host-side
+ * bank simulator built on this call checks which accesses are conflict-free.
+ * Errors: NQ_EINVAL for any argument out of range (block a multiple of 32 in
+ * 32..1024, slots 1..64).
+ */
+int nq_stack_offset(int layout, int block, int slots, int thread, int slot, int field,
+                    uint32_t *offset_out);
+
+/* ------------------------------------------------------------------------- */
+/* Multi-worker split (Section 4.5).                                          */
+/* ------------------------------------------------------------------------- */
+
+/*
+ * Static split of n subproblems, in canonical order, across k workers
+ * (1..4096), each worker's share a contiguous slice [first[i], first[i] +
+ * count[i]) (caller-owned host arrays of k entries). With ratios (k floats in
+ * 0..1; the last one is not used) worker i < k-1 gets the single-precision
+ * product ratios[i] x n truncated to an integer -- the rule that reproduces
+ * the per-GPU subproblem counts of the paper's 27-Queens run log -- and worker
+ * k-1 the remainder. ratios == NULL is the uniform split (Table 7's "equal
+ * number of subproblems"): n / k each (integer division), the remainder to
+ * the last worker. NQ_EINVAL for k out of range, a ratio outside 0..1 or not
+ * finite, or shares that add up to more than n.
+ */
+int nq_partition(uint64_t n, const float *ratios, int k, uint64_t *first, uint64_t *count);
+
 /* Name of a status code (static string). */
 const char *nq_strerror(int code);
 

@@ -61,6 +61,25 @@ struct SearchArgs {
     uint32_t mul[4];
 };
 
+// Shared-memory stack geometry (Section 3.1's conflict-free layout, in the
+// form every kernel here uses): slot k of thread t lives at byte
+// (k * block + t) * elem of its array, elem = 16 for whole frames
+// {cols, ld, rd, avail} and 4 for the four separate 32-bit arrays (WT32),
+// which follow each other every slots * block * 4 bytes. One definition for
+// the kernels and for nq_stack_offset, so host-side bank checks test the
+// addresses the kernels use.
+__host__ __device__ constexpr uint32_t stack_elem_bytes(bool split_arrays) {
+    return split_arrays ? 4u : 16u;
+}
+__host__ __device__ constexpr uint32_t stack_slot_offset(uint32_t block, uint32_t thread,
+                                                         uint32_t slot, uint32_t elem) {
+    return (slot * block + thread) * elem;
+}
+__host__ __device__ constexpr uint32_t stack_array_bytes(uint32_t block, uint32_t slots,
+                                                         uint32_t elem) {
+    return slots * block * elem;
+}
+
 // Constrained mode packs the row index of a frame into bits 27..31 of cols.
 constexpr int kRowShift = 27;
 constexpr int kMaxConstrainedN = 26;

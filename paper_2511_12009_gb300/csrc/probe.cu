@@ -1,4 +1,6 @@
-// probe.cu -- integer-pipe throughput microbenchmark (the roofline's denominator).
+// probe.cu -- microbenchmarks behind the roofline: the integer pipes' issue
+// rate (the denominator) and a shared-memory access pattern probe (for
+// reading the profiler's bank-conflict counters on a known pattern).
 //
 // Every thread runs 8 independent dependency chains of one 32-bit integer
 // instruction, written as hand-written inline PTX from the PTX ISA, so the
@@ -65,6 +67,78 @@ void *probe_ptr() {
     return reinterpret_cast<void *>(&alu_probe<KIND>);
 }
 
+extern __shared__ __align__(16) unsigned char probe_smem[];
+
+// Shared-memory pattern probe. Each iteration every lane of `lane_mask` picks
+// a pseudo-random stack slot and, if it is active, makes one access:
+//   KIND 0  16-byte load   of its frame, frames interleaved by thread (the
+//           search kernel's layout: slot k of thread t at (k * block + t) * 16)
+//   KIND 1  16-byte store  to the same addresses
+//   KIND 2  4-byte load    from 32-bit words interleaved by thread (WT32)
+//   KIND 3  16-byte load   with each thread's frames contiguous (slot k of
+//           thread t at (t * slots + k) * 16): the per-thread stack of a
+//           plain port, which puts the 8 lanes of a phase on the same banks
+//           whenever their stacks are a multiple of 128 bytes apart
+// A lane is active when its bit of lane_mask is set and, for density < 32,
+// when the iteration's hash draws below density/32. The loaded words are
+// folded into a value written out so that no access is dead.
+template <int KIND>
+__global__ void smem_probe(uint32_t *out, int iters, uint32_t lane_mask, int density, int slots,
+                           uint32_t seed) {
+    const uint32_t t = threadIdx.x, lane = t & 31u, block = blockDim.x;
+    const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(probe_smem);
+    const uint32_t elem = KIND == 2 ? nqi::stack_elem_bytes(true) : nqi::stack_elem_bytes(false);
+    for (int k = 0; k < slots; ++k) {
+        const uint32_t a = KIND == 3 ? (t * (uint32_t)slots + (uint32_t)k) * 16u
+                                     : nqi::stack_slot_offset(block, t, (uint32_t)k, elem);
+        const uint32_t v = t * 977u + (uint32_t)k;
+        if (KIND == 2)
+            asm volatile("st.shared.u32 [%0], %1;" : : "r"(sbase + a), "r"(v) : "memory");
+        else
+            asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};" : : "r"(sbase + a), "r"(v)
+                         : "memory");
+    }
+    __syncthreads();
+    const bool in_mask = (lane_mask >> lane) & 1u;
+    uint32_t h = (seed ^ (blockIdx.x * 0x9E3779B9u)) + t * 0x85EBCA6Bu;
+    uint32_t acc = 0;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            h ^= h << 13; h ^= h >> 17; h ^= h << 5;  // xorshift32
+            const bool on = in_mask && (density >= 32 || (int)(h & 31u) < density);
+            const uint32_t k = (h >> 8) % (uint32_t)slots;
+            const uint32_t a = sbase + (KIND == 3 ? (t * (uint32_t)slots + k) * 16u
+                                                  : nqi::stack_slot_offset(block, t, k, elem));
+            const uint32_t p = on ? 1u : 0u;
+            if (KIND == 1) {
+                asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t"
+                             "@q st.shared.v4.u32 [%1], {%2, %2, %2, %2};\n\t}"
+                             : : "r"(p), "r"(a), "r"(acc ^ h) : "memory");
+                acc += h;
+            } else if (KIND == 2) {
+                uint32_t x = 0;
+                asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %1, 0;\n\t"
+                             "@q ld.shared.u32 %0, [%2];\n\t}"
+                             : "+r"(x) : "r"(p), "r"(a) : "memory");
+                acc += x;
+            } else {
+                uint32_t x = 0, y = 0, z = 0, w = 0;
+                asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %4, 0;\n\t"
+                             "@q ld.shared.v4.u32 {%0, %1, %2, %3}, [%5];\n\t}"
+                             : "+r"(x), "+r"(y), "+r"(z), "+r"(w) : "r"(p), "r"(a) : "memory");
+                acc += x ^ y ^ z ^ w;
+            }
+        }
+    }
+    out[blockIdx.x * blockDim.x + t] = acc;
+}
+
+template <int KIND>
+void *smem_probe_ptr() {
+    return reinterpret_cast<void *>(&smem_probe<KIND>);
+}
+
 }  // namespace
 
 /*
@@ -123,5 +197,53 @@ extern "C" int nq_probe_alu(int kind, int iters, double *per_clk_per_sm, double 
     cudaEventDestroy(e1);
     cudaFree(out);
     cudaFree(cyc);
+    return rc;
+}
+
+/*
+ * Shared-memory pattern probe (see smem_probe above): one launch of
+ * SMs x resident blocks x 256 threads, `slots` stack slots per thread, iters x 8
+ * accesses per lane. Writes the launch's CUDA-event time in milliseconds.
+ * Synchronous; allocates and frees its own output buffer.
+ */
+extern "C" int nq_probe_smem(int kind, uint32_t lane_mask, int density, int iters, int slots,
+                             double *ms_out) {
+    if (kind < 0 || kind > 3 || density < 0 || density > 32 || iters < 1 || slots < 1 ||
+        slots > 16 || !ms_out)
+        return NQ_EINVAL;
+    void *k = kind == 0 ? smem_probe_ptr<0>() : kind == 1 ? smem_probe_ptr<1>()
+            : kind == 2 ? smem_probe_ptr<2>() : smem_probe_ptr<3>();
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return NQ_ECUDA;
+    const int block = 256;
+    const size_t smem = (size_t)slots * block * 16u;
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess)
+        return NQ_ECUDA;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, smem) != cudaSuccess || nb < 1)
+        return NQ_ECUDA;
+    const int grid = sms * nb;
+    uint32_t *out = nullptr;
+    if (cudaMalloc(&out, (size_t)grid * block * 4) != cudaSuccess) return NQ_ENOMEM;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    uint32_t seed = 0x2545F491u;
+    void *params[] = {&out, &iters, &lane_mask, &density, &slots, &seed};
+    int rc = NQ_OK;
+    cudaEventRecord(e0);
+    if (cudaLaunchKernel(k, dim3(grid), dim3(block), params, smem, nullptr) != cudaSuccess)
+        rc = NQ_ECUDA;
+    cudaEventRecord(e1);
+    if (cudaEventSynchronize(e1) != cudaSuccess) rc = NQ_ECUDA;
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    *ms_out = ms;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
     return rc;
 }

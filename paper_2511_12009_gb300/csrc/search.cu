@@ -423,14 +423,15 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
     constexpr bool kArith = LAYOUT == NQ_LAYOUT_WT32A || kWtm || kRegm;  // alternating sentinel
     constexpr bool kRegs = kReg || kWt || kWt32 || kWtm;  // top frame held in registers
     static_assert(kReg || !CONSTR, "constrained mode uses the REG layout");
-    constexpr uint32_t kElem = kWt32 ? 4u : 16u;  // bytes of one slot in one array
+    constexpr uint32_t kElem = stack_elem_bytes(kWt32);  // bytes of one slot in one array
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(nq_smem);
     Lane k;
-    k.stride = blockDim.x * kElem;
-    k.base = sbase + threadIdx.x * kElem;
+    k.stride = stack_slot_offset(blockDim.x, 0u, 1u, kElem);
+    k.base = sbase + stack_slot_offset(blockDim.x, threadIdx.x, 0u, kElem);
     k.limit = k.base + (uint32_t)a.slots * k.stride;
     // WT32: bytes per array; constrained mode: address of allowed[] after the stacks
-    k.table = kWt32 ? (uint32_t)a.slots * k.stride : sbase + (uint32_t)a.slots * k.stride;
+    const uint32_t arr = stack_array_bytes(blockDim.x, (uint32_t)a.slots, kElem);
+    k.table = kWt32 ? arr : sbase + arr;
     k.thr = 0;
     const unsigned lane = threadIdx.x & 31u;
     const unsigned lt_mask = (1u << lane) - 1u;
@@ -848,8 +849,8 @@ __device__ __forceinline__ uint32_t ld_cg1(const void *p) {
 __global__ void __maxnreg__(64) serve_kernel(const ServeArgs a) {
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(nq_smem);
     Lane k;
-    k.stride = blockDim.x * 16u;
-    k.base = sbase + threadIdx.x * 16u;
+    k.stride = stack_slot_offset(blockDim.x, 0u, 1u, stack_elem_bytes(false));
+    k.base = sbase + stack_slot_offset(blockDim.x, threadIdx.x, 0u, stack_elem_bytes(false));
     k.limit = k.base + (uint32_t)a.slots * k.stride;
     const uint32_t tables = sbase + (uint32_t)a.slots * k.stride;   // nslots x 128 B
     const uint32_t gens = tables + (uint32_t)a.nslots * 128u;        // nslots x 4 B

@@ -86,6 +86,11 @@ def _declare(lib):
                                          ctypes.POINTER(ctypes.c_float)]),
         "nq_batch_counts": (_i32, [_vp, _i32, _vp, _u64, ctypes.POINTER(_u64)]),
         "nq_batch_destroy": (None, [_vp]),
+        "nq_probe_smem": (_i32, [_i32, ctypes.c_uint32, _i32, _i32, _i32,
+                                 ctypes.POINTER(ctypes.c_double)]),
+        "nq_stack_offset": (_i32, [_i32, _i32, _i32, _i32, _i32, _i32,
+                                   ctypes.POINTER(ctypes.c_uint32)]),
+        "nq_partition": (_i32, [_u64, _vp, _i32, _vp, _vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -273,6 +278,40 @@ def probe_alu(kind: int, iters: int = 4096) -> dict:
     _check(lib().nq_probe_alu(int(kind), int(iters), ctypes.byref(a), ctypes.byref(b),
                               ctypes.byref(c)), "nq_probe_alu")
     return {"per_clk_per_sm": a.value, "per_s": b.value, "sm_mhz": c.value}
+
+
+def probe_smem(kind: int, lane_mask: int = 0xFFFFFFFF, density: int = 32, iters: int = 256,
+               slots: int = 8) -> float:
+    """Shared-memory pattern probe (nq_probe_smem); returns the launch time in ms."""
+    ms = ctypes.c_double()
+    _check(lib().nq_probe_smem(int(kind), int(lane_mask) & 0xFFFFFFFF, int(density), int(iters),
+                               int(slots), ctypes.byref(ms)), "nq_probe_smem")
+    return ms.value
+
+
+def stack_offset(layout, block: int, slots: int, thread: int, slot: int, field: int) -> int:
+    """Byte offset of a stack word in the search kernel's shared memory (nq_stack_offset)."""
+    if isinstance(layout, str):
+        layout = LAYOUTS[layout]
+    out = ctypes.c_uint32()
+    _check(lib().nq_stack_offset(int(layout), int(block), int(slots), int(thread), int(slot),
+                                 int(field), ctypes.byref(out)), "nq_stack_offset")
+    return int(out.value)
+
+
+def partition(n: int, k: int, ratios=None) -> list[tuple[int, int]]:
+    """Static split of n subproblems over k workers (nq_partition): [(first, count)]."""
+    first = np.zeros(max(k, 1), dtype=np.uint64)
+    count = np.zeros(max(k, 1), dtype=np.uint64)
+    rp = None
+    if ratios is not None:
+        r = np.ascontiguousarray(np.asarray(ratios, dtype=np.float32))
+        if len(r) != k:
+            raise ValueError("one ratio per worker")
+        rp = r.ctypes.data
+    _check(lib().nq_partition(int(n), rp, int(k), first.ctypes.data, count.ctypes.data),
+           "nq_partition")
+    return [(int(f), int(c)) for f, c in zip(first, count)]
 
 
 def header_symbols() -> list[str]:
