@@ -397,6 +397,9 @@ int nq_probe_alu(int kind, int iters, double *per_clk_per_sm, double *per_s, dou
  *   kind 2  4-byte load, 32-bit words interleaved by thread (WT32)
  *   kind 3  16-byte load, each thread's frames contiguous (slot k of thread t
  *           at (t x slots + k) x 16): a per-thread stack, the counter-example
+ *   kind 4  8-byte load, 8-byte words interleaved by thread ((k x 256 + t) x 8)
+ *   kind 5  8-byte store, same addresses
+ *   kind 6  4-byte store, 32-bit words interleaved by thread (WT32)
  * ms_out = CUDA-event time of the launch. Synchronous; allocates and frees its
  * own output buffer.
  */

@@ -79,6 +79,10 @@ extern __shared__ __align__(16) unsigned char probe_smem[];
 //           thread t at (t * slots + k) * 16): the per-thread stack of a
 //           plain port, which puts the 8 lanes of a phase on the same banks
 //           whenever their stacks are a multiple of 128 bytes apart
+//   KIND 4  8-byte load    from 8-byte words interleaved by thread (slot k of
+//           thread t at (k * block + t) * 8)
+//   KIND 5  8-byte store   to the same addresses
+//   KIND 6  4-byte store   to 32-bit words interleaved by thread (WT32)
 // A lane is active when its bit of lane_mask is set and, for density < 32,
 // when the iteration's hash draws below density/32. The loaded words are
 // folded into a value written out so that no access is dead.
@@ -87,13 +91,16 @@ __global__ void smem_probe(uint32_t *out, int iters, uint32_t lane_mask, int den
                            uint32_t seed) {
     const uint32_t t = threadIdx.x, lane = t & 31u, block = blockDim.x;
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(probe_smem);
-    const uint32_t elem = KIND == 2 ? nqi::stack_elem_bytes(true) : nqi::stack_elem_bytes(false);
+    const uint32_t elem = (KIND == 2 || KIND == 6) ? nqi::stack_elem_bytes(true)
+                        : (KIND == 4 || KIND == 5) ? 8u : nqi::stack_elem_bytes(false);
     for (int k = 0; k < slots; ++k) {
         const uint32_t a = KIND == 3 ? (t * (uint32_t)slots + (uint32_t)k) * 16u
                                      : nqi::stack_slot_offset(block, t, (uint32_t)k, elem);
         const uint32_t v = t * 977u + (uint32_t)k;
-        if (KIND == 2)
+        if (KIND == 2 || KIND == 6)
             asm volatile("st.shared.u32 [%0], %1;" : : "r"(sbase + a), "r"(v) : "memory");
+        else if (KIND == 4 || KIND == 5)
+            asm volatile("st.shared.v2.u32 [%0], {%1, %1};" : : "r"(sbase + a), "r"(v) : "memory");
         else
             asm volatile("st.shared.v4.u32 [%0], {%1, %1, %1, %1};" : : "r"(sbase + a), "r"(v)
                          : "memory");
@@ -116,6 +123,22 @@ __global__ void smem_probe(uint32_t *out, int iters, uint32_t lane_mask, int den
                              "@q st.shared.v4.u32 [%1], {%2, %2, %2, %2};\n\t}"
                              : : "r"(p), "r"(a), "r"(acc ^ h) : "memory");
                 acc += h;
+            } else if (KIND == 6) {
+                asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t"
+                             "@q st.shared.u32 [%1], %2;\n\t}"
+                             : : "r"(p), "r"(a), "r"(acc ^ h) : "memory");
+                acc += h;
+            } else if (KIND == 5) {
+                asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %0, 0;\n\t"
+                             "@q st.shared.v2.u32 [%1], {%2, %2};\n\t}"
+                             : : "r"(p), "r"(a), "r"(acc ^ h) : "memory");
+                acc += h;
+            } else if (KIND == 4) {
+                uint32_t x = 0, y = 0;
+                asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %2, 0;\n\t"
+                             "@q ld.shared.v2.u32 {%0, %1}, [%3];\n\t}"
+                             : "+r"(x), "+r"(y) : "r"(p), "r"(a) : "memory");
+                acc += x ^ y;
             } else if (KIND == 2) {
                 uint32_t x = 0;
                 asm volatile("{\n\t.reg .pred q;\n\tsetp.ne.u32 q, %1, 0;\n\t"
@@ -208,11 +231,13 @@ extern "C" int nq_probe_alu(int kind, int iters, double *per_clk_per_sm, double 
  */
 extern "C" int nq_probe_smem(int kind, uint32_t lane_mask, int density, int iters, int slots,
                              double *ms_out) {
-    if (kind < 0 || kind > 3 || density < 0 || density > 32 || iters < 1 || slots < 1 ||
+    if (kind < 0 || kind > 6 || density < 0 || density > 32 || iters < 1 || slots < 1 ||
         slots > 16 || !ms_out)
         return NQ_EINVAL;
     void *k = kind == 0 ? smem_probe_ptr<0>() : kind == 1 ? smem_probe_ptr<1>()
-            : kind == 2 ? smem_probe_ptr<2>() : smem_probe_ptr<3>();
+            : kind == 2 ? smem_probe_ptr<2>() : kind == 3 ? smem_probe_ptr<3>()
+            : kind == 4 ? smem_probe_ptr<4>() : kind == 5 ? smem_probe_ptr<5>()
+            : smem_probe_ptr<6>();
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess ||
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)

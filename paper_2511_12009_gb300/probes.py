@@ -6,7 +6,7 @@
 ``smem`` runs one launch per pattern, in the order of CASES, and prints one JSON
 line per launch with what a conflict-free access pattern needs: for each warp
 instruction, the phases with at least one active lane (128-bit accesses are
-served 8 lanes per phase, 32-bit accesses 32 lanes per phase) and the fewest
+served 8 lanes per phase, 64-bit 16, 32-bit 32) and the fewest
 wavefronts the active lanes' bytes could take (ceil(active bytes / 128)). Read
 beside a profiler's shared-memory wavefront and bank-conflict counters for the
 same launches, these tell bank conflicts (distinct words on one bank within a
@@ -33,6 +33,13 @@ CASES = [
     (2, 0xFFFFFFFF, 32, "4-byte loads, split arrays, all lanes"),
     (2, 0xFFFFFFFF, 8, "4-byte loads, split arrays, each lane active with p = 1/4"),
     (3, 0xFFFFFFFF, 32, "16-byte loads, per-thread contiguous stacks, all lanes"),
+    (4, 0xFFFFFFFF, 32, "8-byte loads, interleaved words, all lanes"),
+    (4, 0x00010001, 32, "8-byte loads, interleaved words, lanes 0 and 16"),
+    (4, 0x000F000F, 32, "8-byte loads, interleaved words, lanes 0-3 and 16-19"),
+    (4, 0xFFFFFFFF, 8, "8-byte loads, interleaved words, each lane active with p = 1/4"),
+    (5, 0xFFFFFFFF, 8, "8-byte stores, interleaved words, each lane active with p = 1/4"),
+    (6, 0xFFFFFFFF, 32, "4-byte stores, split arrays, all lanes"),
+    (6, 0xFFFFFFFF, 8, "4-byte stores, split arrays, each lane active with p = 1/4"),
 ]
 ITERS, SLOTS = 256, 8
 
@@ -44,7 +51,7 @@ def _binom(n: int, k: int, p: float) -> float:
 def expected(kind: int, mask: int, density: int) -> dict:
     """Per warp instruction: mean phases holding an active lane, and mean
     fewest wavefronts for the active bytes (both for a conflict-free pattern)."""
-    width = 4 if kind == 2 else 16
+    width = 4 if kind in (2, 6) else 8 if kind in (4, 5) else 16
     lanes_per_phase = 128 // width
     p = min(density, 32) / 32.0
     phases, ideal = 0.0, 0.0
