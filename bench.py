@@ -305,6 +305,8 @@ def run_served(args, device, local):
     with Server(max_n=20, request_slots=64, idle_ms=200) as srv:
         res = run_stream(srv, sat, timeout_s=3600)
     capacity = len(reqs) / res["wall_s"]
+    print(f"served: saturation run {res['wall_s']:.1f} s, {capacity:.2f} requests/s",
+          file=sys.stderr, flush=True)
     runs = [{"load": "saturation", "wall_s": res["wall_s"],
              "p50_ms": 1e3 * float(np.percentile(list(res["latency_s"].values()), 50)),
              "p99_ms": 1e3 * float(np.percentile(list(res["latency_s"].values()), 99))}]
@@ -317,6 +319,7 @@ def run_served(args, device, local):
         with Server(max_n=20, request_slots=64, idle_ms=200) as srv:
             r = run_stream(srv, stream, timeout_s=3600)
         lat = list(r["latency_s"].values())
+        print(f"served: load {load} run {r['wall_s']:.1f} s", file=sys.stderr, flush=True)
         if r["answers"] != answers:
             raise SystemExit("answers differ between runs")
         runs.append({"load": load, "rate_per_s": rate, "wall_s": r["wall_s"],

@@ -98,7 +98,11 @@ typedef struct nq_queen {
                              integer multiply-adds, balancing the FMA and ALU pipes */
 #define NQ_LAYOUT_REGM 7  /* REG with the same multiply-add arithmetic */
 
-/* Launch configuration. Zero in any field selects the library default. */
+/* Launch configuration. Zero in any field selects the default: for layout,
+ * block, claim and d the environment variables NQ_LAYOUT (a layout number or
+ * name: paper, reg, wt, wt32, wt32a, wtm, regm), NQ_BLOCK, NQ_CLAIM and NQ_D
+ * when set to a valid value, else the library's own default. (Batches take
+ * their configuration as given.) */
 typedef struct nq_config {
     int32_t layout;        /* NQ_LAYOUT_* */
     int32_t block;         /* threads per block, a multiple of 32, <= 1024 */

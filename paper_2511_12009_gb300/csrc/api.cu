@@ -1,11 +1,15 @@
 // api.cu -- the extern "C" entry points of libnq (declared in include/nq.h).
 #include <algorithm>
 #include <chrono>
+#include <cstdlib>
 #include <cstring>
 #include <memory>
 #include <vector>
 
 #include "nq_internal.h"
+#include "prefix.h"
+
+#include <nvtx3/nvToolsExt.h>
 
 using namespace nqi;
 
@@ -20,6 +24,42 @@ double ms_since(Clock::time_point t0) {
 bool aligned(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
 int cuda_rc(cudaError_t e) { return e == cudaSuccess ? NQ_OK : NQ_ECUDA; }
+
+// Host phases show up as named ranges in a timeline profiler (no-ops without one).
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+};
+
+int env_int(const char *name) {
+    const char *v = std::getenv(name);
+    if (!v || !*v) return 0;
+    char *end = nullptr;
+    const long x = std::strtol(v, &end, 10);
+    return (end && *end == '\0' && x > 0 && x < (1L << 30)) ? (int)x : 0;
+}
+
+int env_layout() {
+    const char *v = std::getenv("NQ_LAYOUT");
+    if (!v || !*v) return 0;
+    static const char *names[] = {"default", "paper", "reg", "wt", "wt32", "wt32a", "wtm", "regm"};
+    for (int i = 0; i < 8; ++i)
+        if (std::strcmp(v, names[i]) == 0) return i;
+    const int x = env_int("NQ_LAYOUT");
+    return x <= NQ_LAYOUT_REGM ? x : 0;
+}
+
+// The configuration a call runs with: the caller's fields, and for the ones it
+// leaves at 0 the environment's NQ_LAYOUT (number or name), NQ_BLOCK, NQ_CLAIM
+// and NQ_D, else the library defaults.
+nq_config with_env(const nq_config *cfg) {
+    nq_config c = cfg ? *cfg : nq_config{};
+    if (!c.layout) c.layout = env_layout();
+    if (!c.block) c.block = env_int("NQ_BLOCK");
+    if (!c.claim) c.claim = env_int("NQ_CLAIM");
+    if (!c.d) c.d = env_int("NQ_D");
+    return c;
+}
 
 // Pinned host staging buffer, one per host thread (grown on demand).
 struct PinnedBuf {
@@ -69,11 +109,17 @@ struct CallCtx {
 // Enqueue one search over device-resident prefixes (shared by nq_count*,
 // nq_total_ex, nq_count_constrained and nq_count_split). n_tags > 0: the
 // records are split subproblems whose counts and nodes are added into entry
-// tag of d_counts / d_nodes (zeroed here, n_tags entries).
+// tag of d_counts / d_nodes (zeroed here, n_tags entries). cursor_ext: a work
+// cursor the caller allocated and zeroed in stream order (used unless the
+// launch donates subtrees); NULL: the call allocates its own on `s`.
+// published: streamed input (SearchArgs::published); no donation then.
 int enqueue_search(const nq_prefix *d_prefixes, uint64_t n, int expect_n, int min_d, int max_n,
                    uint64_t *d_counts, uint64_t *d_nodes, uint64_t *d_totals,
-                   const nq_config *cfg, const uint32_t *allowed, cudaStream_t s, Plan *used,
-                   uint64_t n_tags = 0) {
+                   const nq_config *cfg_in, const uint32_t *allowed, cudaStream_t s, Plan *used,
+                   uint64_t n_tags = 0, unsigned long long *cursor_ext = nullptr,
+                   const unsigned long long *published = nullptr) {
+    const nq_config cfg_eff = with_env(cfg_in);
+    const nq_config *cfg = &cfg_eff;
     if (n_tags && !d_counts) return NQ_EINVAL;
     if (n_tags) {
         if (cudaMemsetAsync(d_counts, 0, n_tags * sizeof(uint64_t), s) != cudaSuccess ||
@@ -95,15 +141,17 @@ int enqueue_search(const nq_prefix *d_prefixes, uint64_t n, int expect_n, int mi
     // only when asked for: measured on GB300 it has not paid for its queue
     // traffic yet, so batches short of work are better split on the host
     // (nq_count_split).
-    const bool donate = reg && !constrained && !n_tags && cfg && cfg->donate == 2;
+    const bool donate = reg && !constrained && !n_tags && !published && cfg && cfg->donate == 2;
     if (donate && (rc = make_plan(max_n, min_d, diag, constrained, cfg, &p, true))) return rc;
     const size_t head_bytes = 128 + sizeof(DonateCtl);  // cursor line, counters
     const size_t bytes = donate ? head_bytes + kDonateCap * sizeof(DonateItem) : 64;
+    const bool own = donate || !cursor_ext;
     unsigned char *scratch = nullptr;
-    if (cudaMallocAsync(reinterpret_cast<void **>(&scratch), bytes, s) != cudaSuccess)
+    if (own && cudaMallocAsync(reinterpret_cast<void **>(&scratch), bytes, s) != cudaSuccess)
         return NQ_ENOMEM;
-    unsigned long long *cursor = reinterpret_cast<unsigned long long *>(scratch);
-    rc = cuda_rc(cudaMemsetAsync(scratch, 0, donate ? bytes : 64, s));
+    unsigned long long *cursor =
+        own ? reinterpret_cast<unsigned long long *>(scratch) : cursor_ext;
+    if (own) rc = cuda_rc(cudaMemsetAsync(scratch, 0, donate ? bytes : 64, s));
     if (!rc && donate && d_counts)
         rc = cuda_rc(cudaMemsetAsync(d_counts, 0, n * sizeof(uint64_t), s));
     if (!rc && donate && d_nodes)
@@ -133,9 +181,10 @@ int enqueue_search(const nq_prefix *d_prefixes, uint64_t n, int expect_n, int mi
         a.mul[1] = 2u;
         a.mul[2] = 0xFFFFFFFFu;
         a.mul[3] = 0x80000000u;
+        a.published = published;
         rc = launch_search(a, p, diag, constrained, s);
     }
-    cudaFreeAsync(scratch, s);
+    if (own) cudaFreeAsync(scratch, s);
     if (used) *used = p;
     return rc;
 }
@@ -176,61 +225,155 @@ extern "C" int nq_sync(void *stream) {
     return take_device_status();
 }
 
+// nq_total_ex streams large prefix sets: below this many subproblems the set
+// is written, copied and searched in one go.
+constexpr uint64_t kStreamMin = 1ull << 20;
+constexpr int kStreamPieces = 8;
+
 extern "C" int nq_total_ex(int N, const nq_config *cfg, uint64_t *total_out, uint64_t *nodes_out,
                            nq_timing *timing) {
     const auto t_start = Clock::now();
     if (N < 1 || N > NQ_MAX_N || !total_out) return NQ_EINVAL;
     if (N >= 29) return NQ_EOVERFLOW;  // Q(29) > 2^64 (Section 4.5: int64 ends at N = 28)
-    const int d = (cfg && cfg->d > 0) ? cfg->d : nq_default_depth(N);
+    const nq_config cfg_eff = with_env(cfg);
+    cfg = &cfg_eff;
+    const int d = cfg->d > 0 ? cfg->d : nq_default_depth(N);
     if (d < 0 || d > N) return NQ_EINVAL;
 
-    // a1: host enumeration into pinned staging memory
+    // a1 (counting pass): the set cut at its depth-3 nodes, the size of each part
     const auto t_enum = Clock::now();
-    uint64_t np = 0;
-    int rc = nq_enumerate_prefixes(N, d, nullptr, 0, &np);
+    PrefixCut cut;
+    int rc;
+    {
+        Range r("nq.enumerate.count");
+        rc = cut_prefixes(N, d, &cut);
+    }
     if (rc) return rc;
-    nq_prefix *h_pre = static_cast<nq_prefix *>(t_stage.get((np ? np : 1) * sizeof(nq_prefix)));
-    if (!h_pre) return NQ_ENOMEM;
-    uint64_t got = 0;
-    rc = nq_enumerate_prefixes(N, d, h_pre, np, &got);
-    if (rc) return rc;
-    const double enum_ms = ms_since(t_enum);
+    const uint64_t np = cut.first.back();
+    double enum_ms = ms_since(t_enum);
+
+    // Pieces of whole depth-3 nodes in the kernel's claim order: from the end
+    // of the canonical order (the heavier subtrees) unless index order is
+    // configured. After piece j is copied in, the first pub[j] indices in
+    // claim order may be searched.
+    const bool from_end = cfg->order != 1;
+    const size_t nn = cut.nodes.size();
+    std::vector<std::pair<size_t, size_t>> pieces;  // node ranges, claim order
+    {
+        const int k = np >= kStreamMin ? kStreamPieces : 1;
+        size_t done = 0;  // nodes taken so far (from the chosen end)
+        for (int j = 1; j <= k && done < nn; ++j) {
+            const uint64_t want = (np * (uint64_t)j) / (uint64_t)k;  // records covered after j
+            size_t take = done;
+            auto covered = [&](size_t t) {
+                return from_end ? np - cut.first[nn - t] : cut.first[t];
+            };
+            while (take < nn && (j == k || covered(take) < want)) ++take;
+            if (take == done) continue;
+            pieces.emplace_back(from_end ? nn - take : done, from_end ? nn - done : take);
+            done = take;
+        }
+        if (pieces.empty()) pieces.emplace_back(0, 0);
+    }
+    const size_t npieces = pieces.size();
+    // pinned staging: the records, then the published counts
+    const size_t rec_bytes = ((np ? np : 1) * sizeof(nq_prefix) + 15) / 16 * 16;
+    unsigned char *stage =
+        static_cast<unsigned char *>(t_stage.get(rec_bytes + (npieces + 1) * sizeof(uint64_t)));
+    if (!stage) return NQ_ENOMEM;
+    nq_prefix *h_pre = reinterpret_cast<nq_prefix *>(stage);
+    unsigned long long *h_pub = reinterpret_cast<unsigned long long *>(stage + rec_bytes);
 
     CallCtx ctx;
     if ((rc = ctx.init())) return rc;
     nq_prefix *d_pre = nullptr;
     uint64_t *d_tot = nullptr, *d_nodes = nullptr;
+    unsigned long long *d_ctl = nullptr;  // [0] work cursor, [16] published count
     if ((rc = ctx.alloc(&d_pre, np * sizeof(nq_prefix)))) return rc;
     if ((rc = ctx.alloc(&d_tot, 32 * sizeof(uint64_t)))) return rc;
+    if ((rc = ctx.alloc(&d_ctl, 256))) return rc;
     if (nodes_out && (rc = ctx.alloc(&d_nodes, np * sizeof(uint64_t)))) return rc;
-    cudaEvent_t ev[4];
-    for (auto &e : ev)
-        if (cudaEventCreate(&e) != cudaSuccess) return NQ_ECUDA;
-    struct EvGuard {
+    cudaStream_t cs = nullptr;  // copies and publication
+    cudaEvent_t ev[5] = {};
+    struct Guard {
+        cudaStream_t &cs;
         cudaEvent_t *e;
-        ~EvGuard() {
-            for (int i = 0; i < 4; ++i) cudaEventDestroy(e[i]);
+        ~Guard() {  // runs before ctx frees the buffers the copies may still use
+            if (cs) {
+                cudaStreamSynchronize(cs);
+                cudaStreamDestroy(cs);
+            }
+            for (int i = 0; i < 5; ++i)
+                if (e[i]) cudaEventDestroy(e[i]);
         }
-    } evg{ev};
-
-    // a2: upload; a3-a4: search and per-warp reduction; a5: the weighted total
+    } guard{cs, ev};
+    for (auto &e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            e = nullptr;
+            return NQ_ECUDA;
+        }
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+        cs = nullptr;
+        return NQ_ECUDA;
+    }
+    const bool stream_in = npieces > 1;
     cudaEventRecord(ev[0], ctx.s);
-    rc = cuda_rc(cudaMemcpyAsync(d_pre, h_pre, np * sizeof(nq_prefix), cudaMemcpyHostToDevice,
-                                 ctx.s));
-    if (!rc) rc = cuda_rc(cudaMemsetAsync(d_tot, 0, 32 * sizeof(uint64_t), ctx.s));
-    cudaEventRecord(ev[1], ctx.s);
+    rc = cuda_rc(cudaMemsetAsync(d_tot, 0, 32 * sizeof(uint64_t), ctx.s));
+    if (!rc) rc = cuda_rc(cudaMemsetAsync(d_ctl, 0, 256, ctx.s));
+    if (!rc) rc = cuda_rc(cudaEventRecord(ev[1], ctx.s));
+    if (!rc) rc = cuda_rc(cudaStreamWaitEvent(cs, ev[1], 0));
     Plan p{};
-    if (!rc)
-        rc = enqueue_search(d_pre, np, N, d, N, nullptr, d_nodes, d_tot, cfg, nullptr, ctx.s, &p);
+    // a3-a4: one persistent search over the whole set; with streamed input it
+    // starts now and takes pieces as they are published
+    if (!rc && stream_in)
+        rc = enqueue_search(d_pre, np, N, d, N, nullptr, d_nodes, d_tot, cfg, nullptr, ctx.s, &p,
+                            0, d_ctl, d_ctl + 16);
+    // a1 (writing) + a2 upload, piece by piece
+    uint64_t published = 0;
+    if (!rc) rc = cuda_rc(cudaEventRecord(ev[3], cs));
+    for (size_t j = 0; j < npieces && !rc; ++j) {
+        const auto [lo, hi] = pieces[j];
+        const uint64_t r0 = cut.first[lo], r1 = cut.first[hi];
+        const auto tw = Clock::now();
+        {
+            Range r("nq.enumerate.write");
+            write_prefix_nodes(cut, lo, hi, h_pre, np);
+        }
+        enum_ms += ms_since(tw);
+        Range r("nq.upload");
+        if (r1 > r0)
+            rc = cuda_rc(cudaMemcpyAsync(d_pre + r0, h_pre + r0, (r1 - r0) * sizeof(nq_prefix),
+                                         cudaMemcpyHostToDevice, cs));
+        published += r1 - r0;
+        h_pub[j] = published;
+        if (!rc && stream_in)
+            rc = cuda_rc(cudaMemcpyAsync(d_ctl + 16, h_pub + j, sizeof(uint64_t),
+                                         cudaMemcpyHostToDevice, cs));
+    }
+    if (!rc) rc = cuda_rc(cudaEventRecord(ev[4], cs));
+    if (!rc && !stream_in) {
+        rc = cuda_rc(cudaStreamWaitEvent(ctx.s, ev[4], 0));
+        if (!rc)
+            rc = enqueue_search(d_pre, np, N, d, N, nullptr, d_nodes, d_tot, cfg, nullptr, ctx.s,
+                                &p, 0, d_ctl);
+    }
+    if (rc && stream_in) {
+        // the search is waiting for records that will not come: publish the
+        // whole (zeroed, hence rejected) set so that it ends at once
+        h_pub[npieces] = np;
+        cudaMemsetAsync(d_pre, 0, np * sizeof(nq_prefix), cs);
+        cudaMemcpyAsync(d_ctl + 16, h_pub + npieces, sizeof(uint64_t), cudaMemcpyHostToDevice, cs);
+    }
     cudaEventRecord(ev[2], ctx.s);
+    // a5: the weighted total
     uint64_t tot = 0;
     if (!rc)
         rc = cuda_rc(cudaMemcpyAsync(&tot, d_tot + N, sizeof(uint64_t), cudaMemcpyDeviceToHost,
                                      ctx.s));
-    cudaEventRecord(ev[3], ctx.s);
-    if (cudaStreamSynchronize(ctx.s) != cudaSuccess) return NQ_ECUDA;
-    if (rc) return rc;
+    if (cudaStreamSynchronize(ctx.s) != cudaSuccess || cudaStreamSynchronize(cs) != cudaSuccess)
+        return NQ_ECUDA;
     const int st = take_device_status();
+    if (rc) return rc;
     if (st) return st;
     *total_out = tot;
     if (nodes_out) {
@@ -238,13 +381,15 @@ extern "C" int nq_total_ex(int N, const nq_config *cfg, uint64_t *total_out, uin
         if (np && cudaMemcpy(nodes.data(), d_nodes, np * sizeof(uint64_t),
                              cudaMemcpyDeviceToHost) != cudaSuccess)
             return NQ_ECUDA;
-        uint64_t s = 0;
-        for (uint64_t v : nodes) s += v;
-        *nodes_out = s;
+        uint64_t sum = 0;
+        for (uint64_t v : nodes) sum += v;
+        *nodes_out = sum;
     }
     if (timing) {
+        // upload: first to last copy (overlapping the search when streamed);
+        // kernel: from the search's launch point to its end
         float up = 0, kern = 0;
-        cudaEventElapsedTime(&up, ev[0], ev[1]);
+        cudaEventElapsedTime(&up, ev[3], ev[4]);
         cudaEventElapsedTime(&kern, ev[1], ev[2]);
         timing->enumerate_ms = enum_ms;
         timing->upload_ms = up;
@@ -276,6 +421,8 @@ extern "C" int nq_count_split(const nq_prefix *h_prefixes, uint64_t n, int rows,
     const auto t_start = Clock::now();
     if (!h_counts || (n && !h_prefixes) || rows < -1 || rows > NQ_MAX_N || n > kMaxSplitParents)
         return NQ_EINVAL;
+    const nq_config cfg_eff = with_env(cfg);
+    cfg = &cfg_eff;
     if (h_totals) std::memset(h_totals, 0, 32 * sizeof(uint64_t));
     if (n == 0) {
         if (rows_used) *rows_used = 0;

@@ -60,6 +60,28 @@ struct CWalker {
 };
 }  // namespace
 
+uint64_t count_constrained_prefixes(int N, int d, const uint32_t allowed[32]) {
+    const uint32_t last = (1u << N) - 1u;
+    struct Counter {
+        int d;
+        uint32_t last;
+        const uint32_t *allowed;
+        uint64_t rec(int row, uint32_t cols, uint32_t ld, uint32_t rd) const {
+            if (row == d) return 1;
+            uint32_t av = last & ~(cols | ld | rd) & allowed[row];
+            if (row + 1 == d) return (uint64_t)__builtin_popcount(av);
+            uint64_t n = 0;
+            while (av) {
+                const uint32_t p = av & (0u - av);
+                av ^= p;
+                n += rec(row + 1, cols | p, ((ld | p) << 1) & last, (rd | p) >> 1);
+            }
+            return n;
+        }
+    } c{d, last, allowed};
+    return c.rec(0, 0, 0, 0);
+}
+
 void constrained_prefixes(int N, int d, const uint32_t allowed[32], uint32_t tag,
                           std::vector<nq_prefix> &out) {
     CWalker w{N, d, (1u << N) - 1u, allowed, tag, &out};

@@ -59,7 +59,17 @@ struct SearchArgs {
     // (layout WTM). Passed at run time so that the compiler cannot fold them:
     // the products must be issued as integer multiply-adds on the FMA pipe.
     uint32_t mul[4];
+    // Streamed input (NULL: all n records are in place at launch). The host
+    // copies records in while the kernel runs and then raises *published: the
+    // first *published indices in claim order may be read. A lane whose
+    // claimed index is beyond it idles until the next bookkeeping point;
+    // record loads bypass L1 (a line may have been cached before its copy).
+    const unsigned long long *published;
 };
+// Bookkeeping rounds a lane may wait for an unpublished index (each round is
+// one chunk of idle steps, plus a short sleep once the whole warp waits):
+// several seconds, then NQ_ETIMEOUT.
+constexpr unsigned kMaxPublishWaits = 1u << 24;
 
 // Shared-memory stack geometry (Section 3.1's conflict-free layout, in the
 // form every kernel here uses): slot k of thread t lives at byte
@@ -126,6 +136,9 @@ struct ServeArgs {
     int slots;                       // stack slots per lane
     unsigned int idle_polls;         // empty polls (with back-off) before exiting
     uint32_t mul[4];                 // as in SearchArgs
+    // records published, mirrored in device memory: the host copies it in
+    // after the records themselves, on the same stream
+    const unsigned long long *head;
 };
 
 int launch_serve(const ServeArgs &a, int grid, int block, size_t smem, cudaStream_t s);
@@ -174,5 +187,6 @@ int split_prefixes(const nq_prefix *in, uint64_t n, int rows, std::vector<nq_pre
 int constraint_masks(int N, const nq_queen *q, int k, uint32_t allowed[32], bool *conflict);
 void constrained_prefixes(int N, int d, const uint32_t allowed[32], uint32_t tag,
                           std::vector<nq_prefix> &out);
+uint64_t count_constrained_prefixes(int N, int d, const uint32_t allowed[32]);
 
 }  // namespace nqi

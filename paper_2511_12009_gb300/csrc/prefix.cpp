@@ -8,13 +8,19 @@
 // is also taken, with the row-1 queen restricted to the left of the three
 // columns the centre queen blocks (N/2 - 1 positions, weight 2). Order:
 // depth-first, lowest column first at every row.
+#include <unistd.h>
+
 #include <algorithm>
 #include <atomic>
+#include <condition_variable>
+#include <functional>
+#include <mutex>
 #include <cstring>
 #include <thread>
 #include <vector>
 
 #include "nq_internal.h"
+#include "prefix.h"
 
 namespace nqi {
 
@@ -75,11 +81,9 @@ struct Walker {
     }
 };
 
-// Depth-t nodes of the symmetric tree (their Somers state and row-0 column).
-struct Node {
-    uint32_t cols, ld, rd, col0;
-};
+using Node = PrefixNode;
 
+// Depth-t nodes of the symmetric tree (their Somers state and row-0 column).
 void collect(int n, int d, int t, int row, uint32_t cols, uint32_t ld, uint32_t rd, uint32_t col0,
              std::vector<Node> &v) {
     const uint32_t last = mask_n(n);
@@ -139,20 +143,83 @@ unsigned worker_count() {
     return h ? std::min(h, 64u) : 1u;
 }
 
+// Worker threads kept for the process's lifetime, so that a call does not pay
+// for starting them (nq_total_ex runs several parallel passes per call). One
+// job at a time; a caller that finds the pool busy, or runs in a process forked
+// from the one that started it, uses threads of its own instead.
+class Pool {
+  public:
+    static Pool &get() {
+        static Pool *p = new Pool();  // never destroyed: workers may outlive static teardown
+        return *p;
+    }
+    // Runs work() on the pool's threads and the caller's; false if busy.
+    bool run(const std::function<void()> &work) {
+        if (getpid() != pid_ || !run_mu_.try_lock()) return false;
+        {
+            std::unique_lock<std::mutex> lk(mu_);
+            job_ = &work;
+            active_ = (unsigned)th_.size();
+            ++gen_;
+        }
+        cv_.notify_all();
+        work();
+        {
+            std::unique_lock<std::mutex> lk(mu_);
+            done_.wait(lk, [&] { return active_ == 0; });
+            job_ = nullptr;
+        }
+        run_mu_.unlock();
+        return true;
+    }
+
+  private:
+    Pool() : pid_(getpid()) {
+        const unsigned nw = worker_count();
+        for (unsigned i = 1; i < nw; ++i) th_.emplace_back([this] { loop(); });
+        for (auto &t : th_) t.detach();
+    }
+    void loop() {
+        unsigned seen = 0;
+        for (;;) {
+            const std::function<void()> *job;
+            {
+                std::unique_lock<std::mutex> lk(mu_);
+                cv_.wait(lk, [&] { return gen_ != seen; });
+                seen = gen_;
+                job = job_;
+            }
+            (*job)();
+            std::unique_lock<std::mutex> lk(mu_);
+            if (--active_ == 0) done_.notify_all();
+        }
+    }
+    const pid_t pid_;
+    std::mutex run_mu_, mu_;
+    std::condition_variable cv_, done_;
+    std::vector<std::thread> th_;
+    const std::function<void()> *job_ = nullptr;
+    unsigned active_ = 0, gen_ = 0;
+};
+
 // Run fn(i) for i in [0, n) on the host's cores, pulling indices dynamically.
 template <typename F>
 void parallel_for(size_t n, F fn) {
     std::atomic<size_t> next{0};
-    auto work = [&]() {
+    const std::function<void()> work = [&]() {
         for (;;) {
             const size_t i = next.fetch_add(1);
             if (i >= n) break;
             fn(i);
         }
     };
-    const unsigned nw = n > 64 ? worker_count() : 1u;
+    if (n <= 64) {
+        work();
+        return;
+    }
+    if (Pool::get().run(work)) return;
     std::vector<std::thread> th;
-    for (unsigned i = 1; i < nw; ++i) th.emplace_back(work);
+    for (unsigned i = 1; i < worker_count(); ++i) th.emplace_back(work);
     work();
     for (auto &x : th) x.join();
 }
@@ -173,35 +240,52 @@ extern "C" int nq_default_depth(int N) {
 }
 
 
+namespace nqi {
+
+// The set is split at depth t = min(3, d): every depth-t node counts the
+// prefixes below it (in parallel), and then writes its own contiguous slice.
+// The slices follow the nodes' canonical order, so the result is the same
+// array as one depth-first walk.
+int cut_prefixes(int N, int d, PrefixCut *cut) {
+    if (N < 1 || N > NQ_MAX_N || d < 0 || d > N || !cut) return NQ_EINVAL;
+    cut->n = N;
+    cut->d = d;
+    cut->t = std::min(3, d);
+    cut->nodes.clear();
+    collect(N, d, cut->t, 0, 0, 0, 0, 0, cut->nodes);
+    cut->first.assign(cut->nodes.size() + 1, 0);
+    parallel_for(cut->nodes.size(), [&](size_t i) {
+        const Node &v = cut->nodes[i];
+        cut->first[i + 1] = count_below(N, d, cut->t, v.cols, v.ld, v.rd, v.col0);
+    });
+    for (size_t i = 0; i < cut->nodes.size(); ++i) cut->first[i + 1] += cut->first[i];
+    return NQ_OK;
+}
+
+void write_prefix_nodes(const PrefixCut &cut, size_t lo, size_t hi, nq_prefix *out,
+                        uint64_t cap) {
+    if (hi > cut.nodes.size()) hi = cut.nodes.size();
+    if (lo >= hi) return;
+    parallel_for(hi - lo, [&](size_t j) {
+        const size_t i = lo + j;
+        if (cut.first[i] >= cap) return;
+        const Node &v = cut.nodes[i];
+        Walker w{cut.n, cut.d, mask_n(cut.n), true, 0, out + cut.first[i], cap - cut.first[i], 0};
+        w.rec(cut.t, v.cols, v.ld, v.rd, v.col0);
+    });
+}
+
+}  // namespace nqi
+
 extern "C" int nq_enumerate_prefixes(int N, int d, nq_prefix *out, uint64_t cap, uint64_t *n_out) {
     if (N < 1 || N > NQ_MAX_N || d < 0 || d > N || !n_out) return NQ_EINVAL;
-    if (d < 5) {
-        Walker w{N, d, mask_n(N), true, 0, out, out ? cap : 0, 0};
-        w.rec(0, 0, 0, 0, 0);
-        *n_out = w.count;
-        return (out && w.count > cap) ? NQ_EOVERFLOW : NQ_OK;
-    }
-    // Large sets: split at depth t = 3, count below every depth-t node in
-    // parallel, then let each node write its own contiguous slice. The slices
-    // follow the nodes' canonical order, so the result is the same array.
-    const int t = 3;
-    std::vector<Node> nodes;
-    collect(N, d, t, 0, 0, 0, 0, 0, nodes);
-    std::vector<uint64_t> first(nodes.size() + 1, 0);
-    parallel_for(nodes.size(), [&](size_t i) {
-        const Node &v = nodes[i];
-        first[i + 1] = count_below(N, d, t, v.cols, v.ld, v.rd, v.col0);
-    });
-    for (size_t i = 0; i < nodes.size(); ++i) first[i + 1] += first[i];
-    const uint64_t total = first.back();
+    PrefixCut cut;
+    const int rc = cut_prefixes(N, d, &cut);
+    if (rc) return rc;
+    const uint64_t total = cut.first.back();
     *n_out = total;
     if (!out) return NQ_OK;
-    parallel_for(nodes.size(), [&](size_t i) {
-        if (first[i] >= cap) return;
-        const Node &v = nodes[i];
-        Walker w{N, d, mask_n(N), true, 0, out + first[i], cap - first[i], 0};
-        w.rec(t, v.cols, v.ld, v.rd, v.col0);
-    });
+    write_prefix_nodes(cut, 0, cut.nodes.size(), out, cap);
     return total > cap ? NQ_EOVERFLOW : NQ_OK;
 }
 

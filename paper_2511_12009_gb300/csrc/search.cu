@@ -554,12 +554,23 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
                     }
                 }
             }
+            if (a.published) {
+                // streamed input: the claim-order prefix published so far; a
+                // lane whose claimed index lies beyond it waits (idle) for a round
+                unsigned long long v = 0;
+                if (lane == 0)
+                    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v)
+                                 : "l"(a.published) : "memory");
+                v = __shfl_sync(~0u, v, 0);
+                if (need && next_i >= (uint64_t)v) need = false;
+            }
             if (need) {
                 const uint64_t my = next_i++;
                 --rem;
                 {
                     const uint64_t pi = a.order ? a.n - 1 - my : my;
-                    const uint4 P = __ldg(reinterpret_cast<const uint4 *>(a.pre) + pi);
+                    const uint4 P = a.published ? ldcg4(reinterpret_cast<const uint4 *>(a.pre) + pi)
+                                                : __ldg(reinterpret_cast<const uint4 *>(a.pre) + pi);
                     const uint32_t n = (P.w >> 2) & 31u, d = (P.w >> 7) & 31u, w = P.w & 3u;
                     const uint32_t last = (n >= 1u) ? (0xFFFFFFFFu >> (32u - n)) : 0u;
                     const bool ok = n >= 1u && (a.expect_n == 0 || (int)n == a.expect_n) &&
@@ -617,6 +628,24 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
                 }
             }
             need_mask = __ballot_sync(~0u, need);
+        }
+        if (a.published) {
+            // Bounded wait for the host to publish; a warp with nothing else to
+            // do sleeps briefly between looks. A waiting lane holds a claimed
+            // index but no subproblem, so its solution counter is free: it
+            // counts the rounds waited (reset when the lane starts its next
+            // subproblem).
+            const bool pending = idx == kNone && !exhausted;
+            sol = pending ? sol + 1u : sol;
+            if (pending && sol > kMaxPublishWaits) {
+                record_error(NQ_ETIMEOUT);
+                exhausted = true;
+                rem = 0;
+                sol = 0;
+            }
+            if (__all_sync(~0u, pending || (exhausted && idx == kNone)) &&
+                __any_sync(~0u, pending))
+                __nanosleep(256);
         }
         if (donating) {
             // ---- subtree donation, once the main queue is exhausted ----------
@@ -869,6 +898,10 @@ __global__ void __maxnreg__(64) serve_kernel(const ServeArgs a) {
     uint32_t cur_w = 1;  // symmetry weight of the record being searched
     uint64_t sol = 0;
     unsigned int idle_polls = 0;
+    // Claim back-off (warp-uniform): after a claim that found the ring empty
+    // the warp skips its next `skip` claim rounds, doubling up to 64, so that
+    // lanes still searching are not held up by lookups that find nothing.
+    uint32_t backoff = 0, skip = 0;
 
     auto finish_slot = [&](int slot, uint64_t s) {
         if (s) atomicAdd(&a.slot_total[slot], (unsigned long long)s);
@@ -899,17 +932,24 @@ __global__ void __maxnreg__(64) serve_kernel(const ServeArgs a) {
         bool need = idle;
         unsigned need_mask = __ballot_sync(~0u, need);
         bool stopping = false;
-        if (need_mask) {  // one read of the mapped flag per warp
+        if (need_mask == ~0u) {  // the mapped stop flag, read only by an all-idle warp
             int st = 0;
             if (lane == 0) st = a.ctl->stop;
             stopping = __shfl_sync(~0u, st, 0) != 0;
+        }
+        if (skip && need_mask != ~0u) {
+            --skip;
+            need_mask = 0;
         }
         while (need_mask && !stopping) {
             const int leader = __ffs(need_mask) - 1;
             unsigned long long first = 0, got = 0;
             if ((int)lane == leader) {
-                const unsigned long long h = a.ctl->head;
-                unsigned long long cur = atomicAdd(a.cursor, 0ull);
+                unsigned long long h, cur;
+                asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(h) : "l"(a.head)
+                             : "memory");
+                asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(cur) : "l"(a.cursor)
+                             : "memory");
                 for (int t = 0; t < 64 && cur < h; ++t) {
                     const unsigned long long want =
                         h - cur < (unsigned long long)__popc(need_mask) ? h - cur
@@ -926,7 +966,12 @@ __global__ void __maxnreg__(64) serve_kernel(const ServeArgs a) {
             }
             first = __shfl_sync(~0u, first, leader);
             got = __shfl_sync(~0u, got, leader);
-            if (got == 0) break;
+            if (got == 0) {
+                backoff = backoff ? (backoff < 64u ? 2u * backoff : 64u) : 1u;
+                skip = backoff;
+                break;
+            }
+            backoff = 0;
             const unsigned rank = __popc(need_mask & lt_mask);
             if (need && rank < got) {
                 const unsigned long long idx = first + rank;

@@ -23,6 +23,11 @@ using nqi::ServeControl;
 using nqi::ServeDone;
 using nqi::ServeSlot;
 
+// Device control words: the claim cursor at [0], the head mirror on its own
+// 128-byte line at [kHeadWord].
+constexpr size_t kCtlBytes = 256;
+constexpr size_t kHeadWord = 16;
+
 struct nq_server {
     nq_server_config cfg{};
     int dev = 0;
@@ -85,6 +90,7 @@ int ensure_running(nq_server *s) {
     a.ring = s->d_ring;
     a.ring_mask = s->mask;
     a.cursor = s->d_cursor;
+    a.head = s->d_cursor + kHeadWord;
     a.ctl = s->d_ctl;
     a.slot_info = s->d_slot;
     a.slot_total = s->d_total;
@@ -151,7 +157,7 @@ extern "C" int nq_server_create(const nq_server_config *cfg, nq_server **out) {
                              &s->stack_slots);
     }
     if (!rc && (cudaMalloc(&s->d_ring, s->ring * sizeof(nq_prefix)) != cudaSuccess ||
-                cudaMalloc(&s->d_cursor, sizeof(unsigned long long)) != cudaSuccess ||
+                cudaMalloc(&s->d_cursor, kCtlBytes) != cudaSuccess ||
                 cudaMalloc(&s->d_slot, c.request_slots * sizeof(ServeSlot)) != cudaSuccess ||
                 cudaMalloc(&s->d_total, c.request_slots * sizeof(unsigned long long)) !=
                     cudaSuccess ||
@@ -167,7 +173,7 @@ extern "C" int nq_server_create(const nq_server_config *cfg, nq_server **out) {
                 cudaStreamCreateWithFlags(&s->kstream, cudaStreamNonBlocking) != cudaSuccess ||
                 cudaStreamCreateWithFlags(&s->cstream, cudaStreamNonBlocking) != cudaSuccess ||
                 cudaEventCreateWithFlags(&s->kdone, cudaEventDisableTiming) != cudaSuccess ||
-                cudaMemset(s->d_cursor, 0, sizeof(unsigned long long)) != cudaSuccess ||
+                cudaMemset(s->d_cursor, 0, kCtlBytes) != cudaSuccess ||
                 cudaMemset(s->d_slot, 0, c.request_slots * sizeof(ServeSlot)) != cudaSuccess))
         rc = NQ_ECUDA;
     if (rc) {
@@ -210,8 +216,30 @@ extern "C" int nq_server_submit(nq_server *s, int N, const nq_queen *q, int k, u
             break;
         }
     if (slot < 0) return NQ_EBUSY;
-    // the request's depth: at least what fits the kernel's stack, at most N
-    const int d = std::min(N, std::max(N - 1 - s->stack_slots, std::min(N - 2 < 0 ? 0 : N - 2, 5)));
+    // The request's depth: at least what fits the kernel's stack (N - 1 - d
+    // frames), then deeper while its subproblems are fewer than four per
+    // resident lane -- a few heavy subtrees would leave most lanes idle while
+    // they finish -- as long as the next depth's records take at most a
+    // quarter of the ring.
+    int d = std::min(N, std::max(N - 1 - s->stack_slots, std::min(N - 2 < 0 ? 0 : N - 2, 5)));
+    {
+        auto count_at = [&](int dd) -> uint64_t {
+            uint64_t np = 0;
+            if (k == 0) {
+                if (nq_enumerate_prefixes(N, dd, nullptr, 0, &np)) return ~0ull;
+                return np;
+            }
+            return nqi::count_constrained_prefixes(N, dd, allowed);
+        };
+        const uint64_t lanes = (uint64_t)s->grid * (uint64_t)s->block;
+        uint64_t cnt = count_at(d);
+        while (d + 1 <= N - 2 && cnt < 4 * lanes) {
+            const uint64_t next = count_at(d + 1);
+            if (next > s->ring / 4) break;
+            ++d;
+            cnt = next;
+        }
+    }
     std::vector<nq_prefix> pre;
     if (k == 0) {
         // no queen given: the symmetric prefix set of Section 1 (weights 1 or 2)
@@ -257,13 +285,18 @@ extern "C" int nq_server_submit(nq_server *s, int N, const nq_queen *q, int k, u
         ok = ok && cudaMemcpyAsync(s->d_ring, pre.data() + first_part,
                                    (m - first_part) * sizeof(nq_prefix), cudaMemcpyHostToDevice,
                                    s->cstream) == cudaSuccess;
+    // publish: the head's device mirror is copied in after the records, on the
+    // same stream (the copy reads the pinned control block)
+    const uint64_t new_head = s->head + m;
+    s->h_ctl->head = new_head;
+    std::atomic_thread_fence(std::memory_order_seq_cst);
+    ok = ok && cudaMemcpyAsync(s->d_cursor + kHeadWord,
+                               const_cast<unsigned long long *>(&s->h_ctl->head),
+                               sizeof(unsigned long long), cudaMemcpyHostToDevice,
+                               s->cstream) == cudaSuccess;
     ok = ok && cudaStreamSynchronize(s->cstream) == cudaSuccess;
     if (!ok) return NQ_ECUDA;
-    // publish
-    s->head += m;
-    std::atomic_thread_fence(std::memory_order_seq_cst);
-    s->h_ctl->head = s->head;
-    std::atomic_thread_fence(std::memory_order_seq_cst);
+    s->head = new_head;
     s->req[slot].ticket = tk;
     s->req[slot].end = s->head;
     s->req[slot].active = true;

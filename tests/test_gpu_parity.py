@@ -95,6 +95,34 @@ def test_total_public_entry(n):
     assert nq.total(n) == Q[n]
 
 
+@pytest.mark.parametrize("n,d", [(16, 8), (17, 6), (18, 8), (12, 9), (13, 13), (19, 4), (11, 1)])
+def test_total_ex_pieces(n, d):
+    """nq_total_ex writes, uploads and searches large prefix sets in pieces
+    (heaviest first, one stream each); small sets in one piece. Every depth,
+    including the deepest (the whole board placed) and one row (odd N: the centre prefix
+    alone has weight 1), gives Q(N)."""
+    r = nq.total_ex(n, nq.make_config(d=d))
+    assert r["total"] == Q[n] and r["prefixes"] == nq.prefix_count(n, d)
+
+
+def test_environment_defaults(monkeypatch):
+    """Unset configuration fields take NQ_LAYOUT / NQ_BLOCK / NQ_D from the
+    environment; fields the caller sets win; bad values are ignored."""
+    monkeypatch.setenv("NQ_LAYOUT", "reg")
+    monkeypatch.setenv("NQ_BLOCK", "128")
+    monkeypatch.setenv("NQ_D", "6")
+    r = nq.total_ex(16)
+    assert (r["total"], r["layout"], r["block"], r["d"]) == (Q[16], 2, 128, 6)
+    r = nq.total_ex(16, nq.make_config("wt", 256, d=5))
+    assert (r["total"], r["layout"], r["block"], r["d"]) == (Q[16], 3, 256, 5)
+    monkeypatch.setenv("NQ_LAYOUT", "no-such-layout")
+    monkeypatch.setenv("NQ_BLOCK", "-5")
+    monkeypatch.delenv("NQ_D")
+    r = nq.total_ex(16)
+    assert (r["total"], r["layout"], r["block"]) == (Q[16], 7, 256)
+    assert r["d"] == nq.default_depth(16)
+
+
 @pytest.mark.parametrize("layout", LAYOUTS)
 def test_launch_shapes(orc, layout):
     """Block sizes, blocks per SM and claim order do not change any count."""

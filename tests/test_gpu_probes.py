@@ -30,6 +30,6 @@ def test_smem_probe_runs(kind, mask, density):
 
 def test_smem_probe_rejects_bad_arguments():
     with pytest.raises(nq.NQError):
-        nq.probe_smem(4)
+        nq.probe_smem(7)
     with pytest.raises(nq.NQError):
         nq.probe_smem(0, slots=17)
