@@ -312,8 +312,9 @@ typedef struct nq_server_config {
                                request's prefix depth d is raised until N-1-d frames fit */
     int32_t block;          /* threads per block (0: 256) */
     uint64_t ring_records;  /* subproblem ring capacity, a power of two >= 1024 (0: 2^25) */
-    uint32_t idle_ms;       /* the kernel exits after about this long with nothing to do
-                               (bounded wait); the next submit or poll relaunches it (0: 200) */
+    uint32_t idle_ms;       /* the kernel exits once every warp has had nothing to do for
+                               about this long (bounded wait; at most 10 minutes); the next
+                               submit or poll relaunches it (0: 200) */
     int32_t reserved[3];
 } nq_server_config;
 

@@ -133,7 +133,7 @@ int enqueue_search(const nq_prefix *d_prefixes, uint64_t n, int expect_n, int mi
     const bool diag = d_nodes != nullptr;
     const bool constrained = allowed != nullptr;
     Plan p;
-    int rc = make_plan(max_n, min_d, diag, constrained, cfg, &p);
+    int rc = make_plan(max_n, min_d, diag, constrained, cfg, &p, false, published != nullptr);
     if (rc) return rc;
     // Scratch: the work cursor, and with donation its counters and item ring.
     const bool reg = p.layout == NQ_LAYOUT_REG || p.layout == NQ_LAYOUT_REGM;
@@ -316,7 +316,10 @@ extern "C" int nq_total_ex(int N, const nq_config *cfg, uint64_t *total_out, uin
         cs = nullptr;
         return NQ_ECUDA;
     }
-    const bool stream_in = npieces > 1;
+    // streamed input needs a register-stack layout (the default); any other
+    // layout searches once every piece is in
+    const int lay = cfg->layout ? cfg->layout : NQ_LAYOUT_REGM;
+    const bool stream_in = npieces > 1 && (lay == NQ_LAYOUT_REG || lay == NQ_LAYOUT_REGM);
     cudaEventRecord(ev[0], ctx.s);
     rc = cuda_rc(cudaMemsetAsync(d_tot, 0, 32 * sizeof(uint64_t), ctx.s));
     if (!rc) rc = cuda_rc(cudaMemsetAsync(d_ctl, 0, 256, ctx.s));
@@ -533,7 +536,23 @@ extern "C" int nq_count_constrained(int N, const nq_queen *q, int k, uint64_t *c
         *count_out = 0;
         return NQ_OK;
     }
-    const int d = nq_default_depth(N);
+    // Depth: the default, then deeper while the subproblems are fewer than four
+    // per resident lane (queens given in the first rows leave few, heavy
+    // subtrees), up to 2^26 records.
+    int d = std::min(nq_default_depth(N), N);
+    {
+        Plan p{};
+        int prc = make_plan(N, d, false, true, nullptr, &p);
+        if (prc) return prc;
+        const uint64_t lanes = (uint64_t)p.grid * (uint64_t)p.block;
+        uint64_t cnt = count_constrained_prefixes(N, d, allowed);
+        while (d + 1 <= N - 2 && cnt < 4 * lanes) {
+            const uint64_t next = count_constrained_prefixes(N, d + 1, allowed);
+            if (next > (1ull << 26)) break;
+            ++d;
+            cnt = next;
+        }
+    }
     std::vector<nq_prefix> pre;
     constrained_prefixes(N, d, allowed, 0, pre);
     if (pre.empty()) {

@@ -139,6 +139,15 @@ struct ServeArgs {
     // records published, mirrored in device memory: the host copies it in
     // after the records themselves, on the same stream
     const unsigned long long *head;
+    // Idle exit by consensus (device words, zeroed before each launch): a
+    // warp idle for idle_polls rounds counts itself into *idle_warps; when
+    // every warp that has started (*started_warps) is counted, the first to
+    // see it sets *closing, no warp claims again, and all leave. Warps never
+    // leave alone while others still search (the next requests would then
+    // find only a few warps resident).
+    unsigned int *idle_warps;
+    unsigned int *started_warps;
+    unsigned int *closing;
 };
 
 int launch_serve(const ServeArgs &a, int grid, int block, size_t smem, cudaStream_t s);
@@ -154,6 +163,7 @@ struct Plan {
     size_t smem;    // dynamic shared memory per block, bytes
     int sms;        // multiprocessors of the device
     bool donate;    // the kernel variant with subtree donation
+    bool stream;    // the kernel variant for streamed input (SearchArgs::published)
 };
 
 // Stack slots a layout needs for prefixes of depth >= min_d on boards <= max_n
@@ -162,7 +172,7 @@ int slots_needed(int layout, int max_n, int min_d);
 
 // Resolve cfg (may be NULL) into a launch shape for the current device.
 int make_plan(int max_n, int min_d, bool diag, bool constrained, const nq_config *cfg, Plan *plan,
-              bool donate = false);
+              bool donate = false, bool stream = false);
 
 // Enqueue the search kernel. Returns NQ_OK or NQ_ECUDA.
 int launch_search(const SearchArgs &a, const Plan &p, bool diag, bool constrained, cudaStream_t s);

@@ -413,7 +413,7 @@ __device__ __forceinline__ void step_paper(uint32_t &top, const Lane &k, uint32_
     }
 }
 
-template <int LAYOUT, bool DIAG, bool CONSTR, bool DONATE>
+template <int LAYOUT, bool DIAG, bool CONSTR, bool DONATE, bool STREAM = false>
 __device__ __forceinline__ void search_body(const SearchArgs &a) {
     constexpr bool kRegm = LAYOUT == NQ_LAYOUT_REGM;
     constexpr bool kReg = LAYOUT == NQ_LAYOUT_REG || kRegm;
@@ -554,7 +554,7 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
                     }
                 }
             }
-            if (a.published) {
+            if (STREAM) {
                 // streamed input: the claim-order prefix published so far; a
                 // lane whose claimed index lies beyond it waits (idle) for a round
                 unsigned long long v = 0;
@@ -569,8 +569,8 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
                 --rem;
                 {
                     const uint64_t pi = a.order ? a.n - 1 - my : my;
-                    const uint4 P = a.published ? ldcg4(reinterpret_cast<const uint4 *>(a.pre) + pi)
-                                                : __ldg(reinterpret_cast<const uint4 *>(a.pre) + pi);
+                    const uint4 P = STREAM ? ldcg4(reinterpret_cast<const uint4 *>(a.pre) + pi)
+                                           : __ldg(reinterpret_cast<const uint4 *>(a.pre) + pi);
                     const uint32_t n = (P.w >> 2) & 31u, d = (P.w >> 7) & 31u, w = P.w & 3u;
                     const uint32_t last = (n >= 1u) ? (0xFFFFFFFFu >> (32u - n)) : 0u;
                     const bool ok = n >= 1u && (a.expect_n == 0 || (int)n == a.expect_n) &&
@@ -629,7 +629,7 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
             }
             need_mask = __ballot_sync(~0u, need);
         }
-        if (a.published) {
+        if (STREAM) {
             // Bounded wait for the host to publish; a warp with nothing else to
             // do sleeps briefly between looks. A waiting lane holds a claimed
             // index but no subproblem, so its solution counter is free: it
@@ -857,9 +857,11 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
 // the slot's allowed-column masks are cached per block in shared memory and
 // refreshed by generation number. The lane that finishes a slot's last
 // subproblem publishes the slot's total to mapped host memory. Every wait is
-// bounded: the claim retries a fixed number of times, and a warp with nothing
-// to do polls the ring at most idle_polls times (with back-off) before it
-// exits, so the kernel always ends by itself once the host stops feeding it.
+// bounded: the claim retries a fixed number of times; a warp with nothing to
+// do polls the ring with back-off, counts itself idle after idle_polls rounds,
+// and the grid leaves together once every started warp is idle (or after 64x
+// that many rounds in any case), so the kernel always ends by itself once the
+// host stops feeding it.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint4 ld_cg4(const void *p) {
     uint4 v;
@@ -898,6 +900,8 @@ __global__ void __maxnreg__(64) serve_kernel(const ServeArgs a) {
     uint32_t cur_w = 1;  // symmetry weight of the record being searched
     uint64_t sol = 0;
     unsigned int idle_polls = 0;
+    bool counted = false;  // warp-uniform: this warp is in *idle_warps
+    if (lane == 0) atomicAdd(a.started_warps, 1u);
     // Claim back-off (warp-uniform): after a claim that found the ring empty
     // the warp skips its next `skip` claim rounds, doubling up to 64, so that
     // lanes still searching are not held up by lookups that find nothing.
@@ -941,6 +945,13 @@ __global__ void __maxnreg__(64) serve_kernel(const ServeArgs a) {
             --skip;
             need_mask = 0;
         }
+        if (need_mask && !stopping) {  // the grid is leaving: claim nothing more
+            unsigned int cl = 0;
+            if (lane == 0)
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cl) : "l"(a.closing)
+                             : "memory");
+            stopping = __shfl_sync(~0u, cl, 0) != 0;
+        }
         while (need_mask && !stopping) {
             const int leader = __ffs(need_mask) - 1;
             unsigned long long first = 0, got = 0;
@@ -972,6 +983,11 @@ __global__ void __maxnreg__(64) serve_kernel(const ServeArgs a) {
                 break;
             }
             backoff = 0;
+            if (counted) {  // back to work: out of the idle count
+                if (lane == 0) atomicSub(a.idle_warps, 1u);
+                counted = false;
+                idle_polls = 0;
+            }
             const unsigned rank = __popc(need_mask & lt_mask);
             if (need && rank < got) {
                 const unsigned long long idx = first + rank;
@@ -1027,9 +1043,26 @@ __global__ void __maxnreg__(64) serve_kernel(const ServeArgs a) {
                 if (lane == 0) a.ctl->exit_reason = 1;
                 break;
             }
-            if (++idle_polls > a.idle_polls) {
-                if (lane == 0) a.ctl->exit_reason = 2;
-                break;
+            ++idle_polls;
+            if (idle_polls > a.idle_polls && !counted) {
+                if (lane == 0) atomicAdd(a.idle_warps, 1u);
+                counted = true;
+            }
+            if (counted) {
+                int leave = 0;
+                if (lane == 0) {
+                    unsigned int iw, sw;
+                    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(iw)
+                                 : "l"(a.idle_warps) : "memory");
+                    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(sw)
+                                 : "l"(a.started_warps) : "memory");
+                    leave = iw >= sw || (unsigned long long)idle_polls > 64ull * a.idle_polls;
+                    if (leave) {
+                        atomicExch(a.closing, 1u);
+                        a.ctl->exit_reason = 2;
+                    }
+                }
+                if (__shfl_sync(~0u, leave, 0)) break;
             }
             __nanosleep(idle_polls < 64 ? 256u : 4096u);
             continue;
@@ -1053,6 +1086,13 @@ __global__ void __maxnreg__(64) search_kernel_donate(const SearchArgs a) {
     search_body<LAYOUT, DIAG, false, true>(a);
 }
 
+// Streamed input (nq_total_ex): a build of its own, so that the plain kernel
+// carries none of the publication checks.
+template <int LAYOUT, bool DIAG>
+__global__ void __maxnreg__(48) search_kernel_stream(const SearchArgs a) {
+    search_body<LAYOUT, DIAG, false, false, true>(a);
+}
+
 template <int LAYOUT, bool DIAG, bool CONSTR, bool DONATE = false>
 void *kernel_ptr() {
     if constexpr (DONATE)
@@ -1061,7 +1101,14 @@ void *kernel_ptr() {
         return reinterpret_cast<void *>(&search_kernel<LAYOUT, DIAG, CONSTR>);
 }
 
-void *pick_kernel(int layout, bool diag, bool constrained, bool donate = false) {
+void *pick_kernel(int layout, bool diag, bool constrained, bool donate = false,
+                  bool stream = false) {
+    if (stream && layout == NQ_LAYOUT_REGM)
+        return diag ? reinterpret_cast<void *>(&search_kernel_stream<NQ_LAYOUT_REGM, true>)
+                    : reinterpret_cast<void *>(&search_kernel_stream<NQ_LAYOUT_REGM, false>);
+    if (stream && layout == NQ_LAYOUT_REG)
+        return diag ? reinterpret_cast<void *>(&search_kernel_stream<NQ_LAYOUT_REG, true>)
+                    : reinterpret_cast<void *>(&search_kernel_stream<NQ_LAYOUT_REG, false>);
     if (constrained)
         return diag ? kernel_ptr<NQ_LAYOUT_REG, true, true>()
                     : kernel_ptr<NQ_LAYOUT_REG, false, true>();
@@ -1102,7 +1149,7 @@ int slots_needed(int layout, int max_n, int min_d) {
 }
 
 int make_plan(int max_n, int min_d, bool diag, bool constrained, const nq_config *cfg,
-              Plan *plan, bool donate) {
+              Plan *plan, bool donate, bool stream) {
     if (max_n < 1 || max_n > NQ_MAX_N || min_d < 0 || min_d > max_n) return NQ_EINVAL;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return NQ_ECUDA;
@@ -1127,7 +1174,10 @@ int make_plan(int max_n, int min_d, bool diag, bool constrained, const nq_config
     }
     p.smem = (size_t)p.block * per_thread + extra;
     p.donate = donate && (p.layout == NQ_LAYOUT_REG || p.layout == NQ_LAYOUT_REGM) && !constrained;
-    void *k = pick_kernel(p.layout, diag, constrained, p.donate);
+    p.stream = stream && !p.donate && !constrained &&
+               (p.layout == NQ_LAYOUT_REG || p.layout == NQ_LAYOUT_REGM);
+    if (stream && !p.stream) return NQ_EINVAL;
+    void *k = pick_kernel(p.layout, diag, constrained, p.donate, p.stream);
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem) !=
         cudaSuccess)
         return NQ_ECUDA;
@@ -1145,7 +1195,8 @@ int make_plan(int max_n, int min_d, bool diag, bool constrained, const nq_config
 int launch_search(const SearchArgs &a, const Plan &p, bool diag, bool constrained,
                   cudaStream_t s) {
     if (a.n == 0) return NQ_OK;
-    void *k = pick_kernel(p.layout, diag, constrained, p.donate && a.dq != nullptr);
+    if ((a.published != nullptr) != p.stream) return NQ_EINVAL;
+    void *k = pick_kernel(p.layout, diag, constrained, p.donate && a.dq != nullptr, p.stream);
     SearchArgs args = a;
     void *params[] = {&args};
     const cudaError_t e = cudaLaunchKernel(k, dim3(p.grid), dim3(p.block), params, p.smem, s);

@@ -3,13 +3,15 @@
 // A request (board size N plus queens that must appear in the solution) is
 // compiled on the host into per-row allowed masks and the prefix rows
 // enumerated under them, tagged with a free request slot, appended to the
-// device ring and published by advancing the ring's head in mapped memory.
-// The persistent kernel picks the new subproblems up while it is still
-// searching older ones. Admission: a request is taken only when a slot is
-// free, the ring has room (ring positions are reused only below the end of
-// the latest completed request: claims are in ring order, so everything
-// below it has been read), and its stack footprint fits the running kernel's
-// (its prefix depth is raised until N - 1 - d frames fit).
+// device ring and published by advancing the ring's head: a copy of the new
+// head into device memory, on the stream that copied the records (the kernel
+// never reads host memory to claim). The persistent kernel picks the new
+// subproblems up while it is still searching older ones. Admission: a request
+// is taken only when a slot is free, the ring has room (ring positions are
+// reused only below the end of the latest completed request: claims are in
+// ring order, so everything below it has been read), and its stack footprint
+// fits the running kernel's (its prefix depth is raised until N - 1 - d frames
+// fit, and further while it has fewer than four subproblems per resident lane).
 #include <algorithm>
 #include <atomic>
 #include <deque>
@@ -23,10 +25,12 @@ using nqi::ServeControl;
 using nqi::ServeDone;
 using nqi::ServeSlot;
 
-// Device control words: the claim cursor at [0], the head mirror on its own
-// 128-byte line at [kHeadWord].
-constexpr size_t kCtlBytes = 256;
+// Device control words, each on its own 128-byte line: the claim cursor at
+// [0] and the head mirror at [kHeadWord] (u64 units), then the idle-exit
+// counters (u32, reset before every launch) from byte kExitBytes on.
+constexpr size_t kCtlBytes = 640;
 constexpr size_t kHeadWord = 16;
+constexpr size_t kExitBytes = 256;
 
 struct nq_server {
     nq_server_config cfg{};
@@ -91,6 +95,12 @@ int ensure_running(nq_server *s) {
     a.ring_mask = s->mask;
     a.cursor = s->d_cursor;
     a.head = s->d_cursor + kHeadWord;
+    unsigned char *exitw = reinterpret_cast<unsigned char *>(s->d_cursor) + kExitBytes;
+    a.idle_warps = reinterpret_cast<unsigned int *>(exitw);
+    a.started_warps = reinterpret_cast<unsigned int *>(exitw + 128);
+    a.closing = reinterpret_cast<unsigned int *>(exitw + 256);
+    if (cudaMemsetAsync(exitw, 0, kCtlBytes - kExitBytes, s->kstream) != cudaSuccess)
+        return NQ_ECUDA;
     a.ctl = s->d_ctl;
     a.slot_info = s->d_slot;
     a.slot_total = s->d_total;
@@ -98,8 +108,9 @@ int ensure_running(nq_server *s) {
     a.done = s->d_done;
     a.nslots = s->cfg.request_slots;
     a.slots = s->stack_slots;
-    // about idle_ms of polling: the back-off sleeps 4 us per poll once idle
-    a.idle_polls = 64u + s->cfg.idle_ms * 250u;
+    // about idle_ms of polling (the back-off sleeps 4 us per poll once idle)
+    // before a warp counts itself idle; idle_ms is capped at 10 minutes
+    a.idle_polls = 64u + std::min(s->cfg.idle_ms, 600000u) * 250u;
     a.mul[0] = 1u;
     a.mul[1] = 2u;
     a.mul[2] = 0xFFFFFFFFu;
