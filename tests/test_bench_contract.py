@@ -1,0 +1,37 @@
+"""bench.py's reference arm runs on the host alone (the oracle on a bounded,
+seeded sample), so its JSON line can be checked here without a GPU; under a
+multi-rank launch only rank 0 prints."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def run_bench(args, env_extra=None):
+    env = dict(os.environ)
+    env.update(env_extra or {})
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py")] + args, cwd=ROOT,
+                       env=env, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    return [json.loads(l) for l in r.stdout.splitlines() if l.startswith("{")]
+
+
+def test_reference_arm_line():
+    lines = run_bench(["--impl", "reference", "--steps", "1", "--warmup", "0", "--n", "12"])
+    assert len(lines) == 1
+    j = lines[0]
+    assert j["impl"] == "reference" and j["unit"] == "nodes/s" and j["value"] > 0
+    assert j["higher_is_better"] is True and j["steps"] == 1 and j["warmup"] == 0
+    assert j["cpu_baseline"]["kind"] == "oracle" and j["cpu_baseline"]["cores"] >= 1
+    assert j["cpu_baseline"]["value"] == j["value"] and j["cpu_baseline"]["sample"]
+    assert j["e2e"] == {"value": j["value"], "unit": j["unit"], "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+    assert j["config"]["n"] == 12 and j["vs_baseline"] is None
+
+
+def test_reference_arm_other_ranks_print_nothing():
+    lines = run_bench(["--impl", "reference", "--steps", "1", "--warmup", "0", "--n", "12"],
+                      {"WORLD_SIZE": "2", "RANK": "1", "LOCAL_RANK": "1"})
+    assert lines == []

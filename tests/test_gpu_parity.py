@@ -184,6 +184,52 @@ def test_degenerate_prefixes(orc, layout):
             assert int(tot[n]) == Q[n]
 
 
+def random_placements(n, d, k, seed):
+    """k seeded random non-attacking placements of rows 0..d-1 on an n x n board
+    (each row a uniform choice among its free columns, restarting at a dead end)."""
+    g = synth_inputs.SplitMix64(seed)
+    out = []
+    while len(out) < k:
+        placed = []
+        for r in range(d):
+            free = [c for c in range(n)
+                    if all(c != pc and abs(c - pc) != r - pr for pr, pc in enumerate(placed))]
+            if not free:
+                break
+            placed.append(free[g.below(len(free))])
+        if len(placed) == d:
+            out.append(placed)
+    return out
+
+
+def records_of(n, placements):
+    """Subproblem records (weight 1) from column lists, by the board geometry: a
+    queen at (r, c) attacks row d at c + (d - r) and c - (d - r)."""
+    pre = np.zeros(len(placements), dtype=nq.PREFIX_DTYPE)
+    for i, q in enumerate(placements):
+        d = len(q)
+        pre[i]["cols"] = sum(1 << c for c in q)
+        pre[i]["ld"] = sum(1 << (c + d - r) for r, c in enumerate(q) if c + d - r < n)
+        pre[i]["rd"] = sum(1 << (c - d + r) for r, c in enumerate(q) if c - d + r >= 0)
+        pre[i]["meta"] = 1 | (n << 2) | (d << 7)
+    return pre
+
+
+@pytest.mark.parametrize("layout", ["regm", "reg", "paper"])
+@pytest.mark.parametrize("n", [29, 30, 31])
+def test_widest_boards(orc, layout, n):
+    """The widest boards the 32-bit masks allow (N = 31 leaves one pre-set high
+    column): seeded random prefixes eight rows short of the bottom, counts and
+    nodes per prefix against the oracle."""
+    d = n - 8
+    q = random_placements(n, d, 1536, 3100 + n)
+    cols = np.array(q, dtype=np.int8)
+    want, want_n = orc.count_prefixes(n, cols)
+    got, got_n, tot = run(records_of(n, q), d, n, layout, nodes=True)
+    assert np.array_equal(got, want) and np.array_equal(got_n, want_n)
+    assert int(tot[n]) == int(want.sum())
+
+
 def test_malformed_records_are_rejected():
     pre = nq.enumerate_prefixes(10, 3).copy()
     pre["meta"][5] = (pre["meta"][5] & ~np.uint32(3))          # weight 0
