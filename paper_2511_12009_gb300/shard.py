@@ -110,13 +110,15 @@ class Done:
         hi = lo + len(counts)
         if hi == lo:
             return
-        j = bisect.bisect_right(self.lo, lo)
-        # an overlap with a neighbour must agree on every shared subproblem
-        for k in (j - 1, j):
-            if 0 <= k < len(self.lo) and self.lo[k] < hi and lo < self.hi[k]:
+        # every range it overlaps must agree on the shared subproblems
+        k = max(0, bisect.bisect_right(self.lo, lo) - 1)
+        while k < len(self.lo) and self.lo[k] < hi:
+            if lo < self.hi[k]:
                 a, b = max(lo, self.lo[k]), min(hi, self.hi[k])
-                if not np.array_equal(counts[a - lo:b - lo], self.counts[k][a - self.lo[k]:b - self.lo[k]]):
+                if not np.array_equal(counts[a - lo:b - lo],
+                                      self.counts[k][a - self.lo[k]:b - self.lo[k]]):
                     raise CheckpointError(f"{where}: subproblems {a}..{b - 1} recorded with two counts")
+            k += 1
         # keep only the parts not yet covered
         for a, b in self.missing(lo, hi):
             k = bisect.bisect_right(self.lo, a)
@@ -217,6 +219,11 @@ def count_board(n: int, d: int | None = None, *, rank: int = 0, world: int = 1,
 
     done = read_checkpoint(checkpoint, header) if checkpoint is not None else Done()
     group = dist.is_available() and dist.is_initialized() and world > 1
+    if group and (dist.get_world_size() != world or dist.get_rank() != rank):
+        raise ValueError(f"worker {rank} of {world}, but the process group has rank "
+                         f"{dist.get_rank()} of {dist.get_world_size()}")
+    if not 0 <= rank < world:
+        raise ValueError("rank must be in [0, world)")
     if group:
         dist.barrier()  # every worker has read the logs before anyone appends
     log = _Log(f"{checkpoint}.rank{rank}", header) if checkpoint is not None else None

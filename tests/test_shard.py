@@ -184,6 +184,14 @@ def test_conflicting_records_are_refused():
     assert done.covered() == 4 and done.missing(0, 6) == [(4, 6)]
     with pytest.raises(shard.CheckpointError):
         done.add(1, np.array([9], dtype=np.uint64))
+    # a range spanning several recorded ones is checked against each of them
+    done.add(10, np.array([7, 7], dtype=np.uint64))
+    done.add(20, np.array([5], dtype=np.uint64))
+    with pytest.raises(shard.CheckpointError):  # agrees at 3 and 10..11, not at 20
+        done.add(3, np.array([4] + [0] * 6 + [7, 7] + [0] * 8 + [6], dtype=np.uint64))
+    assert done.missing(0, 22) == [(4, 10), (12, 20), (21, 22)]
+    done.add(3, np.array([4] + [0] * 6 + [7, 7] + [0] * 8 + [5, 0], dtype=np.uint64))
+    assert done.missing(0, 22) == [] and done.covered() == 22
 
 
 def test_single_worker_splits_agree():
