@@ -43,8 +43,8 @@ SM_MAX_MHZ_FALLBACK = 2070.0
 # ncu capture, valid only for the kernel source it was taken on: the sha256 of
 # search.cu and nq_internal.h. Any change to them makes the figure stale, and
 # the roofline then reports traffic as null.
-TRAFFIC_NCU = {"n": 18, "d": 7, "layout": "default", "bytes": 121123328 + 35011072,
-               "kernel_sha256": "78a3ac45a9e19905c068de25f0975259bb1118f1313baf82bac976f114540ccf"}
+TRAFFIC_NCU = {"n": 18, "d": 7, "layout": "default", "bytes": 121763328 + 34925056,
+               "kernel_sha256": "36116bd3a416a6b35e4d1e6472f05657ae13b6c9cb977f0253f89354e512916d"}
 
 
 def parse():

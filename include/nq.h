@@ -413,7 +413,8 @@ int nq_probe_smem(int kind, uint32_t lane_mask, int density, int iters, int slot
 
 /*
  * Byte offset, within a block's dynamic shared memory, of 32-bit field `field`
- * (0 cols, 1 ld, 2 rd, 3 avail) of stack slot `slot` (0 = the sentinel) of
+ * (0 cols, 1 ld, 2 rd, 3 avail) of stack slot `slot` (slot 0 holds a sentinel
+ * frame; REGM's production build keeps a second one in slot 1) of
  * thread `thread`, for a block of `block` threads with `slots` slots per
  * thread, in layout `layout` -- the addresses the search kernel computes (the
  * kernel and this call share one definition). Whole-frame layouts (PAPER, REG,
