@@ -67,7 +67,7 @@ def parse():
                     help="n18: the full N (default 18) count; batched: N=16..21 in one graph "
                          "launch vs one launch each; served: Poisson request stream; "
                          "probe27: 4096 seeded N=27 subtrees")
-    ap.add_argument("--requests", type=int, default=1000, help="served: requests per run")
+    ap.add_argument("--requests", type=int, default=200, help="served: requests per run")
     ap.add_argument("--loads", default="1.0,0.8,0.5", help="served: offered loads (x capacity)")
     return ap.parse_args()
 
