@@ -17,17 +17,36 @@
  * diagonal r + c and anti-diagonal r - c + N - 1, and the search is the
  * textbook row-by-row recursive backtracker.
  *
- * Functions:
- *   orc_brute_perm          all N! permutations, pairwise attack check (pin)
+ * Functions, and what pins each one (tests/test_oracle.py unless noted):
+ *   orc_brute_perm          all N! permutations, pairwise attack check (Section
+ *                           1's definition written out). Pinned against
+ *                           orc_total for N <= 10, which the next pins fix.
  *   orc_total               backtracker over the whole board, no symmetry
- *   orc_count_constrained   backtracker with some rows' columns fixed
+ *                           (Section 1). Pinned by an independent Python
+ *                           permutation count (N <= 7), orc_brute_perm (N <= 10),
+ *                           OEIS A000170 (N <= 13; N <= 16 through the symmetric
+ *                           driver), and its node count by brute force over all
+ *                           partial placements.
+ *   orc_count_constrained   backtracker with some rows' columns fixed (the
+ *                           serving extension; not in the paper). Pinned by
+ *                           brute force with the queens fixed, the eight board
+ *                           symmetries, and k = 0 reducing to orc_total.
  *   orc_prefixes            the symmetric prefix set of Section 1 / Section 2
  *                           (first-row half symmetry and odd-N middle rule) as
- *                           column lists, in the canonical order
- *   orc_prefix_count        the same set's size, without materialising it
- *   orc_prefixes_at_ranks   the prefixes with given canonical indices
+ *                           column lists, in the canonical order. Pinned by a
+ *                           brute-force prefix set, weights summing to the
+ *                           unsymmetric count, and the 27-Queens log's
+ *                           453,688,251 subproblems at d = 7 (Section 4.5).
+ *   orc_prefix_count        the same set's size, without materialising it.
+ *                           Pinned by len(orc_prefixes) and the same log.
+ *   orc_prefixes_at_ranks   the prefixes with given canonical indices. Pinned
+ *                           by indexing orc_prefixes.
  *   orc_count_prefixes      per-prefix solution and node counts, threaded with
- *                           dynamic pulling of prefixes by the worker threads
+ *                           dynamic pulling of prefixes by the worker threads.
+ *                           Pinned by sum of weight x count = Q(N) (OEIS),
+ *                           refinement (a prefix's count and nodes are its
+ *                           children's sums) and mirror invariance.
+ * Parity unpinned: Q(27) (the paper's printed total) is never recomputed.
  *
  * Node: one successful queen placement in a row at or below the prefix depth
  * (rows d..N-1). It does not depend on the order of traversal.
