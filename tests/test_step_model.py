@@ -1,0 +1,120 @@
+"""A step-by-step model of one lane of the default search kernel (layout REGM),
+checked on the CPU against the oracle: the multiply-add form of the step
+(Algorithm 2 with Algorithm 3's last-row rule), the predicated push / save /
+pop tail, the two sentinel frames and the 31-step rounds between bookkeeping
+points. It pins the arithmetic and stack bounds the kernel relies on -- the
+exact sums behind the multiply-adds, N - d stack slots per lane, and an idle
+lane never popping below its stack within a round -- on whole prefix sets,
+not the kernel's code itself (the GPU parity tests do that)."""
+import pytest
+
+from paper_2511_12009_gb300 import nq
+
+M = 0xFFFFFFFF
+STEPS_PER_ROUND = 31
+# the kernel's sentinel frame for the multiply-add layouts
+SENTINEL = (0xAAAAAAAA, 0xAAAAAAAA, 0xAAAAAAAA, 0x55555555)
+
+
+def popc(x):
+    return bin(x).count("1")
+
+
+def step(state, stack, top):
+    """One REGM step: returns (state, top, counted solution). `stack` maps slot
+    index -> saved frame; `top` is the next free slot."""
+    c, l, r, av = state
+    p = av & ((av * M) & M)                      # av & -av
+    ar = (p * M + av) & M                        # av - p
+    c2 = (p + c) & M                             # cols | p
+    l2 = (l * 2 + p * 2) & M                     # (ld | p) << 1
+    r2 = ((((p + r) & M) * 0x80000000) >> 32)    # (rd | p) >> 1, as umulhi
+    a2 = ~(c2 | l2 | r2) & M                     # free columns of the next row
+    plast = popc(c2) == 31
+    pcnt = a2 != 0 and plast
+    ppush = a2 != 0 and not plast
+    psave = ar != 0 and ppush
+    ppop = ar == 0 and not ppush
+    if psave:
+        stack[top] = (c, l, r, ar)
+        top += 1
+    if ppop:
+        top -= 1
+        assert top >= 0, "popped below the stack"
+        c, l, r, av = stack[top]
+    elif ppush:
+        c, l, r, av = c2, l2, r2, a2
+    else:
+        av = ar
+    return (c, l, r, av), top, 1 if pcnt else 0
+
+
+def search(rec, slots):
+    """Solutions and nodes below one record, the lane running whole rounds;
+    also the deepest slot used."""
+    n = (int(rec["meta"]) >> 2) & 31
+    d = (int(rec["meta"]) >> 7) & 31
+    last = (1 << n) - 1
+    c0 = int(rec["cols"]) | (~last & M)
+    l0, r0 = int(rec["ld"]), int(rec["rd"]) & last
+    a0 = ~(c0 | l0 | r0) & M
+    if d == n:
+        return 1, 0, 0
+    if d + 1 == n or a0 == 0:
+        s = popc(a0)
+        return s, s, 0
+    stack = {0: SENTINEL, 1: SENTINEL}
+    state, top = (c0, l0, r0, a0), 2
+    sol = steps = 0
+    deepest = top
+    while True:
+        for _ in range(STEPS_PER_ROUND):
+            if top > 1:        # on the subproblem (top <= 1: idle on a sentinel)
+                steps += 1
+            state, top, s = step(state, stack, top)
+            sol += s
+            deepest = max(deepest, top)
+            assert top <= slots, "a frame was saved beyond the lane's last slot"
+        if top <= 1:           # idle at the bookkeeping point: subproblem done
+            return sol, steps + sol, deepest
+
+
+@pytest.mark.parametrize("n,d", [(6, 2), (8, 3), (9, 4), (10, 3), (10, 6), (11, 5), (7, 7),
+                                 (9, 8)])
+def test_model_equals_oracle(orc, n, d):
+    pre = nq.enumerate_prefixes(n, d)
+    cols, _ = orc.prefixes(n, d)
+    want, want_nodes = orc.count_prefixes(n, cols)
+    slots = max(n - 1 - d, 1) + 1   # the kernel's stack for REGM
+    for i, rec in enumerate(pre):
+        sol, nodes, deepest = search(rec, slots)
+        assert (sol, nodes) == (int(want[i]), int(want_nodes[i])), (n, d, i)
+        assert deepest <= slots      # every saved frame lies in slots 2 .. slots-1
+
+
+def test_idle_lane_lasts_a_round_and_no_more():
+    """From the reset idle state (sentinel in registers, top at slot 1) a lane
+    takes 31 steps without leaving its stack; a 32nd would pop below slot 0."""
+    stack = {0: SENTINEL, 1: SENTINEL}
+    state, top = SENTINEL, 1
+    for _ in range(STEPS_PER_ROUND):
+        state, top, s = step(state, stack, top)
+        assert s == 0 and 0 <= top <= 1
+    with pytest.raises(AssertionError, match="below"):
+        step(state, stack, top)
+
+
+def test_sentinel_never_pushes_or_counts():
+    state, top, stack = SENTINEL, 1, {0: SENTINEL, 1: SENTINEL}
+    for _ in range(16):
+        state, top2, s = step(state, stack, top)
+        assert s == 0 and top2 <= top
+        top = top2
+
+
+def test_slots_bound_is_tight_somewhere(orc):
+    """Some N=10, d=3 subproblem uses every one of the N - d slots, so one slot
+    fewer would overflow."""
+    n, d = 10, 3
+    slots = (n - 1 - d) + 1
+    assert max(search(rec, slots)[2] for rec in nq.enumerate_prefixes(n, d)) == slots
