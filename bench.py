@@ -34,10 +34,29 @@ UNIT = "nodes/s"
 # neg+and (lowest bit), xor (clear it), or (cols), or+shl (ld), or+shr (rd),
 # nor3 (next row) -- the algorithmic work of Algorithm 2's loop body.
 ALU_OPS_PER_NODE = 10
-# 32-bit integer ALU lanes per clock per SM the roofline is drawn against
-# (measured issue rate of the ALU pipe; see nq_probe_alu and the design notes).
-ALU_LANES_PER_CLK_SM = 64
+# The integer roofline. The search issues its 32-bit integer work on two pipes:
+# the ALU pipe (logic, compares, selects, shifts: 64 lanes/clk/SM, measured by
+# nq_probe_alu's lop3/shf rates) and the FMA pipe (the multiply-add form of the
+# disjoint-bit arithmetic and the moves ptxas places there: another 64; the
+# probe's add rate, 127 lanes/clk/SM, is both pipes together). Together they
+# equal the issue rate, 4 warp schedulers x 32 lanes = 128 lanes/clk/SM: the
+# peak integer-op rate of the SM for this instruction mix. The ALU pipe alone
+# is kept beside it as a secondary figure.
+INT_LANES_PER_CLK_SM = 128
+ALU_PIPE_LANES_PER_CLK_SM = 64
 SM_MAX_MHZ_FALLBACK = 2070.0
+# Prefix depth of the library's default (nq_default_depth), restated here so
+# that the reference arm does not load the library: 7 up to N = 22, else 6,
+# never more than N - 2.
+def default_depth(n: int) -> int:
+    return max(0, min(7 if n <= 22 else 6, n - 2))
+
+
+# Search nodes (queen placements in rows 7..21) below the 60,760,010 depth-7
+# prefixes of N = 22, counted by the library's diagnostic kernel build (its
+# per-prefix node counts equal the oracle's on the seeded N = 22 sample and on
+# every prefix of N <= 19); `--n22-nodes` counts them again.
+N22_D7_NODES = 143257329200995
 # DRAM traffic of one production search launch on the default workload (N=18,
 # d=7, default layout), dram__bytes_read.sum + dram__bytes_write.sum from one
 # ncu capture, valid only for the kernel source it was taken on: the sha256 of
@@ -67,6 +86,9 @@ def parse():
                     help="n18: the full N (default 18) count; batched: N=16..21 in one graph "
                          "launch vs one launch each; served: Poisson request stream; "
                          "probe27: 4096 seeded N=27 subtrees")
+    ap.add_argument("--no-n22", action="store_true", help="skip the N=22 solve")
+    ap.add_argument("--n22-nodes", action="store_true",
+                    help="count the N=22 nodes with the diagnostic build (about 2.5 min)")
     ap.add_argument("--requests", type=int, default=200, help="served: requests per run")
     ap.add_argument("--loads", default="1.0,0.8,0.5", help="served: offered loads (x capacity)")
     return ap.parse_args()
@@ -185,6 +207,31 @@ def measured_traffic(n: int, d: int, layout: str):
 
 # --- CPU oracle baseline --------------------------------------------------------
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                v = line.split(":", 1)[1].strip()
+                if v and not v.isdigit():
+                    vendor = ""
+                    for l2 in out.splitlines():
+                        if l2.split(":")[0].strip() == "Vendor ID":
+                            vendor = l2.split(":", 1)[1].strip() + " "
+                    return (vendor + v).strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
 def oracle_rate(n: int, d: int, seconds: float, seed: int = 7) -> dict:
     """The CPU oracle (all host cores, dynamic pulling) on a seeded sample of the
     same workload's subproblems, grown until it has run about `seconds`."""
@@ -203,7 +250,7 @@ def oracle_rate(n: int, d: int, seconds: float, seed: int = 7) -> dict:
         chunk = min(chunk * 2, 65536)
     dt = time.perf_counter() - t0
     return {"value": done_nodes / dt, "unit": UNIT, "cores": oracle.default_threads(),
-            "kind": "oracle", "seconds": dt,
+            "kind": "oracle", "seconds": dt, "cpu_model": cpu_model(),
             "sample": f"{done} seeded-random subproblems of N={n}, d={d} ({done_nodes} nodes)"}
 
 
@@ -212,8 +259,7 @@ def run_reference(args):
     if world > 1 and rank != 0:
         return
     n = args.n
-    from paper_2511_12009_gb300 import nq  # only for the workload's depth
-    d = args.d or nq.default_depth(n)
+    d = args.d or default_depth(n)
     per_step = max(1.0, min(8.0, 120.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
         oracle_rate(n, d, per_step / 4, seed=1)
@@ -230,7 +276,7 @@ def run_reference(args):
             "data": "synthetic", "config": {"workload": f"N={n} full count, d={d} prefixes", "n": n,
                                             "d": d},
             "cpu_baseline": {"kind": "oracle", "cores": rates[0]["cores"], "value": value,
-                             "unit": UNIT,
+                             "unit": UNIT, "cpu_model": cpu_model(),
                              "sample": f"each step: seeded-random subproblems of N={n}, d={d} "
                                        f"for ~{per_step:.0f} s"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -399,6 +445,48 @@ def run_probe27(args, device, local):
     print(json.dumps(line), flush=True)
 
 
+def roofline_of(nodes: int, launch_s: float, sms: int, sm_max_mhz: float) -> dict:
+    """Integer roofline of one search launch: algorithmic 32-bit ops (10 per
+    node) per second against the SM's integer issue capacity."""
+    achieved = nodes * ALU_OPS_PER_NODE / launch_s / 1e12
+    peak = sms * sm_max_mhz * 1e6 * INT_LANES_PER_CLK_SM / 1e12
+    peak_alu = sms * sm_max_mhz * 1e6 * ALU_PIPE_LANES_PER_CLK_SM / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+            "frac": achieved / peak, "traffic": None, "ops_per_node": ALU_OPS_PER_NODE,
+            "nodes_per_launch": nodes,
+            "peak_basis": f"{sms} SMs x {sm_max_mhz:.0f} MHz x {INT_LANES_PER_CLK_SM} int32 "
+                          f"lanes/clk/SM (ALU pipe 64 + FMA pipe 64 = the issue rate)",
+            "peak_alu_pipe": peak_alu, "frac_alu_pipe": achieved / peak_alu}
+
+
+def solve_n22(args, sms: int, sm_max: float, local: int) -> dict:
+    """Q(22) through nq_total_ex with the default configuration: solve time end
+    to end and the search kernel's own time (CUDA events on its stream)."""
+    from paper_2511_12009_gb300 import nq
+    q = json.load(open(os.path.join(ROOT, "tests", "golden", "oeis_a000170.json")))["Q"]
+    nodes = N22_D7_NODES
+    if args.n22_nodes:
+        nodes = nq.total_ex(22, nq.make_config(d=7), nodes=True)["nodes"]
+    clocks = ClockSampler(local)
+    clocks.start()
+    t0 = time.perf_counter()
+    r = nq.total_ex(22)
+    wall = time.perf_counter() - t0
+    clk = clocks.stop()
+    if r["total"] != q["22"]:
+        raise SystemExit(f"N=22 total {r['total']} != {q['22']}")
+    if r["d"] != 7:
+        raise SystemExit("the N=22 node count is for depth 7")
+    kern_s = r["kernel_ms"] * 1e-3
+    return {"total": r["total"], "exact": True, "d": r["d"], "subproblems": r["prefixes"],
+            "solve_ms": 1e3 * wall, "kernel_ms": r["kernel_ms"],
+            "enumerate_ms": r["enumerate_ms"], "nodes": nodes,
+            "nodes_counted_now": bool(args.n22_nodes),
+            "value": nodes / kern_s, "e2e_value": nodes / wall, "unit": UNIT,
+            "roofline": roofline_of(nodes, kern_s, sms, sm_max), "clocks": clk,
+            "paper_ms": 216740, "paper_hw": "1x RTX 4090 (Table 6, best configuration)"}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -512,13 +600,14 @@ def main():
     except (OSError, ValueError):
         pass
     sm_max = float(peaks.get("sm_max_mhz") or clk.get("sm_max_mhz") or SM_MAX_MHZ_FALLBACK)
-    peak_tops = sms * sm_max * 1e6 * ALU_LANES_PER_CLK_SM / 1e12
-    achieved_tops = nodes_per_step * ALU_OPS_PER_NODE / (kern_s_max / args.steps) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved_tops, "peak": peak_tops, "unit": "Tops/s",
-                "frac": achieved_tops / peak_tops, "traffic": measured_traffic(n, d, args.layout),
-                "ops_per_node": ALU_OPS_PER_NODE, "nodes_per_launch": nodes_per_step,
-                "peak_basis": f"{sms} SMs x {sm_max:.0f} MHz x {ALU_LANES_PER_CLK_SM} int32 ALU "
-                              f"lanes/clk/SM"}
+    roofline = roofline_of(nodes_per_step, kern_s_max / args.steps, sms, sm_max)
+    roofline["traffic"] = measured_traffic(n, d, args.layout)
+
+    # N = 22: one exact solve through the public call, timed whole (host
+    # enumeration streamed into the running search, upload, search, total back)
+    n22 = None
+    if rank == 0 and not args.no_n22 and args.n == 18:
+        n22 = solve_n22(args, sms, sm_max, local)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -537,7 +626,7 @@ def main():
                            "parallelism": f"replicas x{world}"},
                 "solve_ms": ms_per_step, "total": total_q, "wall_s": t_wall,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-                "gpu_launches": args.steps}
+                "n22": n22, "gpu_launches": args.steps}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

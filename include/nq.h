@@ -22,10 +22,17 @@
  *     (asynchronous calls: until the stream reaches the call's work).
  *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
  *     stream). Asynchronous entry points enqueue work on it and return; errors
- *     the kernels find are recorded in a per-device status word that
- *     nq_sync() returns and clears.
+ *     the kernels find are recorded in a status word that belongs to that
+ *     stream (one per device context and stream handle), which nq_sync(stream)
+ *     returns and clears. Synchronous entry points, batches and servers record
+ *     into words of their own and return the error themselves. Once 4095
+ *     distinct streams of one context have made asynchronous calls, further
+ *     streams share one overflow word. A status nq_sync has not collected
+ *     stays with the stream handle, also for a later stream that reuses it.
  *   - N is in 1..NQ_MAX_N (bit b of a mask is column b, so N <= 31).
- *   - Thread safety: calls on different streams may run concurrently.
+ *   - Thread safety: calls on different streams may run concurrently, and an
+ *     error found by one stream's work is reported only by that stream's
+ *     nq_sync.
  */
 #ifndef NQ_H
 #define NQ_H
@@ -44,7 +51,8 @@ extern "C" {
 #define NQ_EINVAL (-1)    /* bad argument, malformed prefix record, N mismatch */
 #define NQ_ENOMEM (-2)    /* host or device allocation failed */
 #define NQ_ECUDA (-3)     /* a CUDA runtime call failed (no device, launch error...) */
-#define NQ_EOVERFLOW (-4) /* the result does not fit 64 bits (N >= 29), or a cap was too small */
+#define NQ_EOVERFLOW (-4) /* the result does not fit 64 bits (N >= 29), or a batch exceeds a
+                             fixed capacity */
 #define NQ_ETIMEOUT (-5)  /* a bounded device wait ran out */
 #define NQ_ESTACK (-6)    /* a prefix needs more stack levels than the launch provides */
 #define NQ_EBUSY (-7)     /* the object is in use (e.g. a server slot table is full) */
@@ -144,8 +152,8 @@ typedef struct nq_timing {
  * m with the row-1 queen in columns 0..m-2, weight 2 (weight 1 when d = 1).
  * d = 0 gives the single empty prefix with weight 1.
  * out == NULL: size query, only *n_out is written. If cap is smaller than the
- * set, the first cap records are written, *n_out gets the set's size and
- * NQ_EOVERFLOW is returned. 0 <= d <= N.
+ * set, nothing is written to out, *n_out gets the set's size and NQ_EINVAL is
+ * returned. 0 <= d <= N.
  */
 int nq_enumerate_prefixes(int N, int d, nq_prefix *out, uint64_t cap, uint64_t *n_out);
 
@@ -199,9 +207,10 @@ int nq_count_ex(const nq_prefix *d_prefixes, uint64_t n, int min_d, int max_n,
                 const nq_config *cfg, void *stream);
 
 /*
- * Wait for `stream` and return the first error any kernel of this library
- * recorded on the current device since the last nq_sync (then clear it), or a
- * CUDA error of the stream, or NQ_OK.
+ * Wait for `stream` and return the first error a kernel of this library
+ * recorded for work enqueued on `stream` (nq_count, nq_count_ex) since the
+ * last nq_sync of that stream (then clear it), or a CUDA error of the stream,
+ * or NQ_OK. Other streams' errors are not seen here.
  */
 int nq_sync(void *stream);
 
@@ -289,7 +298,8 @@ int nq_batch_run(nq_batch *b, void *stream, uint64_t *totals_out, float *ms_out)
 int nq_batch_run_separate(nq_batch *b, void *stream, uint64_t *totals_out, float *ms_out);
 
 /* Per-prefix solution counts of board `board` (index into ns) from the last run,
- * in the canonical order of that board's prefix set; size query with h_counts NULL. */
+ * in the canonical order of that board's prefix set; size query with h_counts NULL;
+ * cap below the set's size: NQ_EINVAL, nothing written. */
 int nq_batch_counts(const nq_batch *b, int board, uint64_t *h_counts, uint64_t cap,
                     uint64_t *n_out);
 
@@ -357,17 +367,24 @@ int nq_server_destroy(nq_server *s);
  * arrays -- h_prefixes[n] in, h_counts[n] out (raw solutions per prefix),
  * total_out optional (sum of weight x count) -- and keeps the device side in
  * one fixed static array inside libnq, sized for NQ_NOALLOC_MAX_PREFIXES
- * records (about 6.3 MB, held on every GPU that loads libnq until the
- * process exits). It calls no cudaMalloc, cudaFree or other allocating
- * routine, and creates no stream or event: it works on `stream`
+ * records (about 6.3 MB). It calls no cudaMalloc, cudaFree or other
+ * allocating routine, and creates no stream or event: it works on `stream`
  * (synchronously: results are on the host when it returns).
  *   - n > NQ_NOALLOC_MAX_PREFIXES: returns NQ_EOVERFLOW, nothing is done.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - The first call on a device (in each device context: again after a
+ *     device reset) looks up the array's device address
+ *     (cudaGetSymbolAddress). Under CUDA's lazy module loading that lookup is
+ *     also when the array is committed on the device, where it then stays
+ *     until the process exits; if the device has no room for it the call
+ *     returns NQ_ENOMEM. A process that reserves its memory at start-up
+ *     should make one call with n = 0 then: it commits the array and counts
+ *     nothing. Make that first call before any stream capture.
  *   - Every call reuses the same array and zeroes what must start at zero.
  *     Two calls whose GPU work overlapped would race on it, so each call
- *     holds a process-wide lock until its results are back on the host.
- * Record checks and status codes are those of nq_count.
+ *     holds a process-wide lock until its results are back on the host (also
+ *     when it fails after queueing work: it waits for the stream first).
+ * Record checks and status codes are those of nq_count; the call returns the
+ * kernel's error itself (its error word lives in the array too).
  */
 #define NQ_NOALLOC_MAX_PREFIXES (1u << 18)
 int nq_count_host_noalloc(int N, int d, const nq_prefix *h_prefixes, uint64_t n,

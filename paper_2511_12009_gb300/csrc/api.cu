@@ -113,10 +113,11 @@ struct CallCtx {
 // cursor the caller allocated and zeroed in stream order (used unless the
 // launch donates subtrees); NULL: the call allocates its own on `s`.
 // published: streamed input (SearchArgs::published); no donation then.
+// status: the device word the launch records its first error in.
 int enqueue_search(const nq_prefix *d_prefixes, uint64_t n, int expect_n, int min_d, int max_n,
                    uint64_t *d_counts, uint64_t *d_nodes, uint64_t *d_totals,
                    const nq_config *cfg_in, const uint32_t *allowed, cudaStream_t s, Plan *used,
-                   uint64_t n_tags = 0, unsigned long long *cursor_ext = nullptr,
+                   int *status, uint64_t n_tags = 0, unsigned long long *cursor_ext = nullptr,
                    const unsigned long long *published = nullptr) {
     const nq_config cfg_eff = with_env(cfg_in);
     const nq_config *cfg = &cfg_eff;
@@ -182,6 +183,7 @@ int enqueue_search(const nq_prefix *d_prefixes, uint64_t n, int expect_n, int mi
         a.mul[2] = 0xFFFFFFFFu;
         a.mul[3] = 0x80000000u;
         a.published = published;
+        a.status = status;
         rc = launch_search(a, p, diag, constrained, s);
     }
     if (own) cudaFreeAsync(scratch, s);
@@ -209,20 +211,32 @@ extern "C" int nq_count_ex(const nq_prefix *d_prefixes, uint64_t n, int min_d, i
                            uint64_t *d_counts, uint64_t *d_nodes, uint64_t *d_totals,
                            const nq_config *cfg, void *stream) {
     if (max_n < 1 || max_n > NQ_MAX_N || min_d < 0 || min_d > max_n) return NQ_EINVAL;
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int *status = nullptr;
+    const int rc = stream_status(s, &status);
+    if (rc) return rc;
     return enqueue_search(d_prefixes, n, 0, min_d, max_n, d_counts, d_nodes, d_totals, cfg,
-                          nullptr, static_cast<cudaStream_t>(stream), nullptr);
+                          nullptr, s, nullptr, status);
 }
 
 extern "C" int nq_count(int N, int d, const nq_prefix *d_prefixes, uint64_t n,
                         uint64_t *d_counts, void *stream) {
     if (N < 1 || N > NQ_MAX_N || d < 0 || d > N || !d_counts) return NQ_EINVAL;
-    return enqueue_search(d_prefixes, n, N, d, N, d_counts, nullptr, nullptr, nullptr, nullptr,
-                          static_cast<cudaStream_t>(stream), nullptr);
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int *status = nullptr;
+    const int rc = stream_status(s, &status);
+    if (rc) return rc;
+    return enqueue_search(d_prefixes, n, N, d, N, d_counts, nullptr, nullptr, nullptr, nullptr, s,
+                          nullptr, status);
 }
 
 extern "C" int nq_sync(void *stream) {
-    if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) return NQ_ECUDA;
-    return take_device_status();
+    const cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaStreamSynchronize(s) != cudaSuccess) return NQ_ECUDA;
+    int *status = nullptr;
+    const int rc = stream_status(s, &status);
+    if (rc) return rc;
+    return take_status(status, s);
 }
 
 // nq_total_ex streams large prefix sets: below this many subproblems the set
@@ -288,7 +302,7 @@ extern "C" int nq_total_ex(int N, const nq_config *cfg, uint64_t *total_out, uin
     if ((rc = ctx.init())) return rc;
     nq_prefix *d_pre = nullptr;
     uint64_t *d_tot = nullptr, *d_nodes = nullptr;
-    unsigned long long *d_ctl = nullptr;  // [0] work cursor, [16] published count
+    unsigned long long *d_ctl = nullptr;  // [0] work cursor, [16] published count, [24] status
     if ((rc = ctx.alloc(&d_pre, np * sizeof(nq_prefix)))) return rc;
     if ((rc = ctx.alloc(&d_tot, 32 * sizeof(uint64_t)))) return rc;
     if ((rc = ctx.alloc(&d_ctl, 256))) return rc;
@@ -328,9 +342,10 @@ extern "C" int nq_total_ex(int N, const nq_config *cfg, uint64_t *total_out, uin
     Plan p{};
     // a3-a4: one persistent search over the whole set; with streamed input it
     // starts now and takes pieces as they are published
+    int *d_status = reinterpret_cast<int *>(d_ctl + 24);
     if (!rc && stream_in)
         rc = enqueue_search(d_pre, np, N, d, N, nullptr, d_nodes, d_tot, cfg, nullptr, ctx.s, &p,
-                            0, d_ctl, d_ctl + 16);
+                            d_status, 0, d_ctl, d_ctl + 16);
     // a1 (writing) + a2 upload, piece by piece
     uint64_t published = 0;
     if (!rc) rc = cuda_rc(cudaEventRecord(ev[3], cs));
@@ -358,7 +373,7 @@ extern "C" int nq_total_ex(int N, const nq_config *cfg, uint64_t *total_out, uin
         rc = cuda_rc(cudaStreamWaitEvent(ctx.s, ev[4], 0));
         if (!rc)
             rc = enqueue_search(d_pre, np, N, d, N, nullptr, d_nodes, d_tot, cfg, nullptr, ctx.s,
-                                &p, 0, d_ctl);
+                                &p, d_status, 0, d_ctl);
     }
     if (rc && stream_in) {
         // the search is waiting for records that will not come: publish the
@@ -375,7 +390,7 @@ extern "C" int nq_total_ex(int N, const nq_config *cfg, uint64_t *total_out, uin
                                      ctx.s));
     if (cudaStreamSynchronize(ctx.s) != cudaSuccess || cudaStreamSynchronize(cs) != cudaSuccess)
         return NQ_ECUDA;
-    const int st = take_device_status();
+    const int st = take_status(d_status, ctx.s);
     if (rc) return rc;
     if (st) return st;
     *total_out = tot;
@@ -466,7 +481,8 @@ extern "C" int nq_count_split(const nq_prefix *h_prefixes, uint64_t n, int rows,
     if ((rc = ctx.alloc(&d_kids, m * sizeof(nq_prefix)))) return rc;
     if ((rc = ctx.alloc(&d_counts, n * sizeof(uint64_t)))) return rc;
     if (diag && (rc = ctx.alloc(&d_nodes, n * sizeof(uint64_t)))) return rc;
-    if ((rc = ctx.alloc(&d_tot, 32 * sizeof(uint64_t)))) return rc;
+    if ((rc = ctx.alloc(&d_tot, 32 * sizeof(uint64_t) + 16))) return rc;
+    int *d_status = reinterpret_cast<int *>(d_tot + 32);
     cudaEvent_t ev[3];
     for (auto &e : ev)
         if (cudaEventCreate(&e) != cudaSuccess) return NQ_ECUDA;
@@ -480,12 +496,12 @@ extern "C" int nq_count_split(const nq_prefix *h_prefixes, uint64_t n, int rows,
     rc = m ? cuda_rc(cudaMemcpyAsync(d_kids, kids.data(), m * sizeof(nq_prefix),
                                      cudaMemcpyHostToDevice, ctx.s))
            : NQ_OK;
-    if (!rc) rc = cuda_rc(cudaMemsetAsync(d_tot, 0, 32 * sizeof(uint64_t), ctx.s));
+    if (!rc) rc = cuda_rc(cudaMemsetAsync(d_tot, 0, 32 * sizeof(uint64_t) + 16, ctx.s));
     cudaEventRecord(ev[1], ctx.s);
     Plan p{};
     if (!rc)
         rc = enqueue_search(d_kids, m, 0, kid_min_d, max_n, d_counts, d_nodes, d_tot, cfg,
-                            nullptr, ctx.s, &p, n);
+                            nullptr, ctx.s, &p, d_status, n);
     cudaEventRecord(ev[2], ctx.s);
     if (!rc)
         rc = cuda_rc(cudaMemcpyAsync(h_counts, d_counts, n * sizeof(uint64_t),
@@ -498,7 +514,7 @@ extern "C" int nq_count_split(const nq_prefix *h_prefixes, uint64_t n, int rows,
                                      cudaMemcpyDeviceToHost, ctx.s));
     if (cudaStreamSynchronize(ctx.s) != cudaSuccess) return NQ_ECUDA;
     if (rc) return rc;
-    const int st = take_device_status();
+    const int st = take_status(d_status, ctx.s);
     if (st) return st;
     if (diag)
         for (uint64_t i = 0; i < n; ++i) h_nodes[i] += extra[i];
@@ -565,20 +581,21 @@ extern "C" int nq_count_constrained(int N, const nq_queen *q, int k, uint64_t *c
     nq_prefix *d_pre = nullptr;
     uint64_t *d_tot = nullptr;
     if ((rc = ctx.alloc(&d_pre, pre.size() * sizeof(nq_prefix)))) return rc;
-    if ((rc = ctx.alloc(&d_tot, 32 * sizeof(uint64_t)))) return rc;
+    if ((rc = ctx.alloc(&d_tot, 32 * sizeof(uint64_t) + 16))) return rc;
+    int *d_status = reinterpret_cast<int *>(d_tot + 32);
     rc = cuda_rc(cudaMemcpyAsync(d_pre, pre.data(), pre.size() * sizeof(nq_prefix),
                                  cudaMemcpyHostToDevice, ctx.s));
-    if (!rc) rc = cuda_rc(cudaMemsetAsync(d_tot, 0, 32 * sizeof(uint64_t), ctx.s));
+    if (!rc) rc = cuda_rc(cudaMemsetAsync(d_tot, 0, 32 * sizeof(uint64_t) + 16, ctx.s));
     if (!rc)
         rc = enqueue_search(d_pre, pre.size(), N, d, N, nullptr, nullptr, d_tot, nullptr,
-                            allowed, ctx.s, nullptr);
+                            allowed, ctx.s, nullptr, d_status);
     uint64_t tot = 0;
     if (!rc)
         rc = cuda_rc(cudaMemcpyAsync(&tot, d_tot + N, sizeof(uint64_t), cudaMemcpyDeviceToHost,
                                      ctx.s));
     if (cudaStreamSynchronize(ctx.s) != cudaSuccess) return NQ_ECUDA;
     if (rc) return rc;
-    const int st = take_device_status();
+    const int st = take_status(d_status, ctx.s);
     if (st) return st;
     *count_out = tot;
     return NQ_OK;

@@ -30,7 +30,7 @@ struct nq_batch {
     nq_prefix *d_pre = nullptr;
     uint64_t *d_counts = nullptr;
     uint64_t *d_totals = nullptr;
-    unsigned long long *d_cursor = nullptr;
+    unsigned long long *d_cursor = nullptr;  // [0] work cursor; status word at byte 8
     uint64_t *h_totals = nullptr;  // pinned, 32 entries
     nqi::Plan plan{};
     cudaGraph_t graph = nullptr;
@@ -68,6 +68,7 @@ nqi::SearchArgs args_for(const nq_batch *b, const nq_prefix *pre, uint64_t n, in
     a.mul[1] = 2u;
     a.mul[2] = 0xFFFFFFFFu;
     a.mul[3] = 0x80000000u;
+    a.status = reinterpret_cast<int *>(b->d_cursor + 1);
     return a;
 }
 
@@ -147,7 +148,7 @@ extern "C" int nq_batch_create(const int *ns, const int *ds, int k, const nq_con
     if (cudaMalloc(&b->d_pre, (total ? total : 1) * sizeof(nq_prefix)) != cudaSuccess ||
         cudaMalloc(&b->d_counts, (total ? total : 1) * sizeof(uint64_t)) != cudaSuccess ||
         cudaMalloc(&b->d_totals, 32 * sizeof(uint64_t)) != cudaSuccess ||
-        cudaMalloc(&b->d_cursor, sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&b->d_cursor, 64) != cudaSuccess ||
         cudaMallocHost(&b->h_totals, 32 * sizeof(uint64_t)) != cudaSuccess) {
         release(b);
         return NQ_ENOMEM;
@@ -170,7 +171,7 @@ extern "C" int nq_batch_create(const int *ns, const int *ds, int k, const nq_con
     }
     const nqi::SearchArgs a = args_for(b, b->d_pre, b->n, 0, b->min_d, b->plan.slots);
     bool ok = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-    ok = ok && cudaMemsetAsync(b->d_cursor, 0, sizeof(unsigned long long), s) == cudaSuccess;
+    ok = ok && cudaMemsetAsync(b->d_cursor, 0, 16, s) == cudaSuccess;  // cursor and status
     ok = ok && cudaMemsetAsync(b->d_totals, 0, 32 * sizeof(uint64_t), s) == cudaSuccess;
     ok = ok && nqi::launch_search(a, b->plan, false, false, s) == NQ_OK;
     ok = ok && cudaMemcpyAsync(b->h_totals, b->d_totals, 32 * sizeof(uint64_t),
@@ -221,7 +222,7 @@ extern "C" int nq_batch_run(nq_batch *b, void *stream, uint64_t *totals_out, flo
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
-    const int st = nqi::take_device_status();
+    const int st = nqi::take_status(reinterpret_cast<int *>(b->d_cursor + 1), s);
     if (st) return st;
     if (ms_out) *ms_out = ms;
     return fill_totals(b, totals_out);
@@ -246,7 +247,8 @@ extern "C" int nq_batch_run_separate(nq_batch *b, void *stream, uint64_t *totals
     }
     int rc = NQ_OK;
     if (cudaEventRecord(e0, s) != cudaSuccess ||
-        cudaMemsetAsync(b->d_totals, 0, 32 * sizeof(uint64_t), s) != cudaSuccess)
+        cudaMemsetAsync(b->d_totals, 0, 32 * sizeof(uint64_t), s) != cudaSuccess ||
+        cudaMemsetAsync(b->d_cursor + 1, 0, sizeof(int), s) != cudaSuccess)  // status
         rc = NQ_ECUDA;
     for (int j = 0; j < b->k && !rc; ++j) {
         const uint64_t n = b->first[j + 1] - b->first[j];
@@ -268,7 +270,7 @@ extern "C" int nq_batch_run_separate(nq_batch *b, void *stream, uint64_t *totals
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
-    const int st = nqi::take_device_status();
+    const int st = nqi::take_status(reinterpret_cast<int *>(b->d_cursor + 1), s);
     if (st) return st;
     if (ms_out) *ms_out = ms;
     return fill_totals(b, totals_out);
@@ -282,7 +284,7 @@ extern "C" int nq_batch_counts(const nq_batch *b, int board, uint64_t *h_counts,
     const uint64_t n = b->first[j + 1] - b->first[j];
     *n_out = n;
     if (!h_counts) return NQ_OK;
-    if (cap < n) return NQ_EOVERFLOW;
+    if (cap < n) return NQ_EINVAL;
     if (n && cudaMemcpy(h_counts, b->d_counts + b->first[j], n * sizeof(uint64_t),
                         cudaMemcpyDeviceToHost) != cudaSuccess)
         return NQ_ECUDA;

@@ -65,6 +65,9 @@ struct SearchArgs {
     // claimed index is beyond it idles until the next bookkeeping point;
     // record loads bypass L1 (a line may have been cached before its copy).
     const unsigned long long *published;
+    // Where the launch records the first error it finds (a device int the
+    // caller zeroed; NULL: errors are not recorded).
+    int *status;
 };
 // Bookkeeping rounds a lane may wait for an unpublished index (each round is
 // one chunk of idle steps, plus a short sleep once the whole warp waits):
@@ -148,6 +151,7 @@ struct ServeArgs {
     unsigned int *idle_warps;
     unsigned int *started_warps;
     unsigned int *closing;
+    int *status;                     // the server's error word (device)
 };
 
 int launch_serve(const ServeArgs &a, int grid, int block, size_t smem, cudaStream_t s);
@@ -177,8 +181,16 @@ int make_plan(int max_n, int min_d, bool diag, bool constrained, const nq_config
 // Enqueue the search kernel. Returns NQ_OK or NQ_ECUDA.
 int launch_search(const SearchArgs &a, const Plan &p, bool diag, bool constrained, cudaStream_t s);
 
-// Read and clear the device-wide status word of the current device (synchronous).
-int take_device_status();
+// Status words (errors the kernels find). An asynchronous call records into
+// the word of its stream (stream_status: one word per context and stream
+// handle, the shared word 0 once kStatusWords streams are in use);
+// synchronous calls, batches and servers use a word of their own.
+// take_status waits for `s`, then reads and clears the word (NQ_OK if none).
+int stream_status(cudaStream_t s, int **out);
+int take_status(int *d_status, cudaStream_t s);
+
+// Id of the current device context (driver entry point; NQ_ECUDA without one).
+int current_context_id(unsigned long long *id);
 
 // Host enumeration helpers (prefix.cpp).
 uint32_t meta_of(int weight, int n, int d);

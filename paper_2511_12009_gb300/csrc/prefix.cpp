@@ -285,8 +285,9 @@ extern "C" int nq_enumerate_prefixes(int N, int d, nq_prefix *out, uint64_t cap,
     const uint64_t total = cut.first.back();
     *n_out = total;
     if (!out) return NQ_OK;
+    if (total > cap) return NQ_EINVAL;  // the caller's buffer is too small: nothing written
     write_prefix_nodes(cut, 0, cut.nodes.size(), out, cap);
-    return total > cap ? NQ_EOVERFLOW : NQ_OK;
+    return NQ_OK;
 }
 
 namespace nqi {
@@ -360,10 +361,15 @@ extern "C" int nq_descendants(const nq_prefix *parent, int rows, nq_prefix *out,
     if (n < 1 || d + rows > n || (w != 1 && w != 2)) return NQ_EINVAL;
     const uint32_t last = mask_n(n);
     if ((parent->cols & ~last) || __builtin_popcount(parent->cols) != d) return NQ_EINVAL;
-    Walker wk{n, d + rows, last, false, w, out, out ? cap : 0, 0};
+    // counting pass first: a buffer that is too small gets nothing written
+    Walker cnt{n, d + rows, last, false, w, nullptr, 0, 0};
+    cnt.rec(d, parent->cols, parent->ld & last, parent->rd & last, 0);
+    *n_out = cnt.count;
+    if (!out) return NQ_OK;
+    if (cnt.count > cap) return NQ_EINVAL;
+    Walker wk{n, d + rows, last, false, w, out, cap, 0};
     wk.rec(d, parent->cols, parent->ld & last, parent->rd & last, 0);
-    *n_out = wk.count;
-    return (out && wk.count > cap) ? NQ_EOVERFLOW : NQ_OK;
+    return NQ_OK;
 }
 
 extern "C" int nq_prefixes_at_ranks(int N, int d, const uint64_t *ranks, uint64_t k,

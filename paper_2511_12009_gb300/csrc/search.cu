@@ -33,13 +33,24 @@
 // column for a row with a given queen; the cells the given queens attack
 // removed elsewhere), the frame's row index rides in bits 27..31 of cols, and
 // the next-row mask is additionally ANDed with allowed[row].
+#include <cuda.h>
+
 #include <cstdio>
+#include <map>
+#include <mutex>
+#include <unordered_map>
+#include <utility>
 
 #include "nq_internal.h"
 
 namespace nqi {
 
-__device__ int g_status;  // first error any launch recorded on this device
+// Status words of asynchronous calls, one per (device, stream) in use: a
+// launch records the first error it finds in its stream's word (synchronous
+// calls, batches and servers bring a word of their own). Word 0 is shared by
+// the streams that arrive after the others have taken every word.
+constexpr int kStatusWords = 4096;
+__device__ int g_stream_status[kStatusWords];
 
 namespace {
 
@@ -56,7 +67,9 @@ static_assert(kChunk < kRowShift, "constrained sentinel holds 27 idle steps");
 
 extern __shared__ __align__(16) unsigned char nq_smem[];
 
-__device__ __forceinline__ void record_error(int code) { atomicCAS(&g_status, 0, code); }
+__device__ __forceinline__ void record_error(int *status, int code) {
+    if (status) atomicCAS(status, 0, code);
+}
 
 // Shared-memory accesses by 32-bit shared-window address (the kernel keeps
 // every stack position as such an address, based at the dynamic array).
@@ -125,6 +138,7 @@ struct Lane {
     uint32_t limit;    // one past this thread's last slot
     uint32_t table;    // WT32: bytes per array; constrained mode: address of allowed[]
     uint32_t thr;      // constrained mode: (N-1) << 27, the last-row threshold
+    int *status;       // where this launch records its first error
 };
 
 // One step, layout REG: the top frame (c, l, r, av) lives in registers, the
@@ -170,7 +184,7 @@ __device__ __forceinline__ void step_reg(uint32_t &c, uint32_t &l, uint32_t &r, 
             sts4(top, make_uint4(c, l, r, ar));
             top += k.stride;
         } else {
-            record_error(NQ_ESTACK);
+            record_error(k.status, NQ_ESTACK);
         }
     }
     if (!push && ar == 0u) {
@@ -179,7 +193,7 @@ __device__ __forceinline__ void step_reg(uint32_t &c, uint32_t &l, uint32_t &r, 
             const uint4 f = lds4(top);
             c = f.x; l = f.y; r = f.z; av = f.w;
         } else {
-            record_error(NQ_ESTACK);
+            record_error(k.status, NQ_ESTACK);
             c = CONSTR ? kSentinelC : MADD ? 0xAAAAAAAAu : ~0u;
             l = r = MADD ? 0xAAAAAAAAu : ~0u;
             av = CONSTR ? kSentinelAvC : MADD ? 0x55555555u : ~0u;
@@ -262,12 +276,12 @@ __device__ __forceinline__ void step_wt(uint32_t &c, uint32_t &l, uint32_t &r, u
             top = nt;
             sts4(top, make_uint4(c, l, r, av));
         } else {
-            record_error(NQ_ESTACK);
+            record_error(k.status, NQ_ESTACK);
         }
     } else {
         if (ar == 0u) {
             if (!DIAG || top > k.base) top -= k.stride;
-            else record_error(NQ_ESTACK);
+            else record_error(k.status, NQ_ESTACK);
         }
         const uint4 f = lds4(top);
         c = f.x; l = f.y; r = f.z;
@@ -320,12 +334,12 @@ __device__ __forceinline__ void step_wt32(uint32_t &c, uint32_t &l, uint32_t &r,
             sts1(top + A, l);
             sts1(top + 2u * A, r);
         } else {
-            record_error(NQ_ESTACK);
+            record_error(k.status, NQ_ESTACK);
         }
     } else {
         if (ar == 0u) {
             if (!DIAG || top > k.base) top -= k.stride;
-            else record_error(NQ_ESTACK);
+            else record_error(k.status, NQ_ESTACK);
         }
         c = lds1(top);
         l = lds1(top + A);
@@ -365,12 +379,12 @@ __device__ __forceinline__ void step_wtm(uint32_t &c, uint32_t &l, uint32_t &r, 
             top = nt;
             sts4(top, make_uint4(c, l, r, av));
         } else {
-            record_error(NQ_ESTACK);
+            record_error(k.status, NQ_ESTACK);
         }
     } else {
         if (ar == 0u) {
             if (!DIAG || top > k.base) top -= k.stride;
-            else record_error(NQ_ESTACK);
+            else record_error(k.status, NQ_ESTACK);
         }
         const uint4 f = lds4(top);
         c = f.x; l = f.y; r = f.z;
@@ -385,7 +399,7 @@ template <bool DIAG>
 __device__ __forceinline__ void step_paper(uint32_t &top, const Lane &k, uint32_t &s32,
                                            uint32_t &n32) {
     if (DIAG && top <= k.base) {
-        record_error(NQ_ESTACK);
+        record_error(k.status, NQ_ESTACK);
         return;
     }
     const uint4 f = lds4(top - k.stride);
@@ -409,7 +423,7 @@ __device__ __forceinline__ void step_paper(uint32_t &top, const Lane &k, uint32_
             sts4(top, make_uint4(c2, l2, r2, a2));
             top += k.stride;
         } else {
-            record_error(NQ_ESTACK);
+            record_error(k.status, NQ_ESTACK);
         }
     }
 }
@@ -441,6 +455,7 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
     const uint32_t arr = stack_array_bytes(blockDim.x, (uint32_t)a.slots, kElem);
     k.table = kWt32 ? arr : sbase + arr;
     k.thr = 0;
+    k.status = a.status;
     const unsigned lane = threadIdx.x & 31u;
     const unsigned lt_mask = (1u << lane) - 1u;
     const uint32_t m1 = a.mul[0], m2 = a.mul[1], mneg = a.mul[2], mhalf = a.mul[3];
@@ -494,7 +509,7 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
             // split subproblems: the count goes to the parent named by the tag
             const uint64_t parent = __ldg(reinterpret_cast<const uint32_t *>(a.pre + i) + 3) >> 12;
             if (parent >= a.n_tags) {
-                record_error(NQ_EINVAL);
+                record_error(k.status, NQ_EINVAL);
             } else if (a.counts && s)
                 atomicAdd(reinterpret_cast<unsigned long long *>(&a.counts[parent]),
                           (unsigned long long)s);
@@ -594,10 +609,10 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
                     // (REG: sentinel + ancestors of rows d..N-3; WT / PAPER: sentinel +
                     // frames of rows d..N-2)
                     if (!ok) {
-                        record_error(NQ_EINVAL);
+                        record_error(k.status, NQ_EINVAL);
                         finish(pi, 0, 0, 0, 0);
                     } else if (d + 1u < n && need_slots > a.slots) {
-                        record_error(NQ_ESTACK);
+                        record_error(k.status, NQ_ESTACK);
                         finish(pi, 0, 0, 0, 0);
                     } else {
                         const uint32_t l0 = P.y;
@@ -651,7 +666,7 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
             const bool pending = idx == kNone && !exhausted;
             sol = pending ? sol + 1u : sol;
             if (pending && sol > kMaxPublishWaits) {
-                record_error(NQ_ETIMEOUT);
+                record_error(k.status, NQ_ETIMEOUT);
                 exhausted = true;
                 rem = 0;
                 sol = 0;
@@ -772,7 +787,7 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
                         while (ldcg4b(&it->info.w) != (uint32_t)j - s0 && ++spins < kReadySpins)
                             __nanosleep(128);
                         if (spins >= kReadySpins) {
-                            record_error(NQ_ETIMEOUT);
+                            record_error(k.status, NQ_ETIMEOUT);
                         } else {
                             const uint32_t keep = df.w & (0u - df.w);
                             const uint32_t give = df.w ^ keep;
@@ -810,7 +825,7 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
                 }
                 done = __shfl_sync(~0u, done, 0);
                 if (done) {
-                    if (done == 2) record_error(NQ_ETIMEOUT);
+                    if (done == 2) record_error(k.status, NQ_ETIMEOUT);
                     break;
                 }
                 // back-off: 0.5 us doubling to 64 us while nothing comes
@@ -900,6 +915,7 @@ __global__ void __maxnreg__(64) serve_kernel(const ServeArgs a) {
     const uint32_t gens = tables + (uint32_t)a.nslots * 128u;        // nslots x 4 B
     k.table = tables;
     k.thr = 0;
+    k.status = a.status;
     for (int i = threadIdx.x; i < a.nslots; i += blockDim.x) sts1(gens + 4u * i, 0xFFFFFFFFu);
     for (int i = threadIdx.x; i < a.nslots * 32; i += blockDim.x) sts1(tables + 4u * i, 0u);
     __syncthreads();
@@ -1013,7 +1029,7 @@ __global__ void __maxnreg__(64) serve_kernel(const ServeArgs a) {
                                 d <= n && (P.x & ~last) == 0u && (uint32_t)__popc(P.x) == d &&
                                 (d + 1u >= n || (int)n - 1 - (int)d <= a.slots);
                 if (!ok) {
-                    record_error(NQ_EINVAL);
+                    record_error(k.status, NQ_EINVAL);
                     if (slot < a.nslots) finish_slot(slot, 0);
                 } else {
                     // the slot's allowed masks, cached in this block's shared memory
@@ -1253,11 +1269,88 @@ int launch_serve(const ServeArgs &a, int grid, int block, size_t smem, cudaStrea
     return e == cudaSuccess ? NQ_OK : NQ_ECUDA;
 }
 
-int take_device_status() {
+int current_context_id(unsigned long long *id) {
+    using GetCurrent = CUresult (*)(CUcontext *);
+    using GetId = CUresult (*)(CUcontext, unsigned long long *);
+    static GetCurrent get_current = nullptr;
+    static GetId get_id = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_current = reinterpret_cast<GetCurrent>(f);
+        f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            get_id = reinterpret_cast<GetId>(f);
+    });
+    if (!get_current || !get_id) return NQ_ECUDA;
+    CUcontext c = nullptr;
+    if (get_current(&c) != CUDA_SUCCESS) return NQ_ECUDA;
+    if (!c) {  // no context current yet: the runtime's primary context of this device
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaSetDevice(dev) != cudaSuccess ||
+            get_current(&c) != CUDA_SUCCESS || !c)
+            return NQ_ECUDA;
+    }
+    return get_id(c, id) == CUDA_SUCCESS ? NQ_OK : NQ_ECUDA;
+}
+
+// Device address of this context's stream status words (looked up once per
+// context: a device reset or a new context gets a fresh lookup).
+int stream_status_words(int **out) {
+    static std::mutex mu;
+    static std::unordered_map<unsigned long long, int *> addr;  // context id -> words
+    unsigned long long ctx = 0;
+    int rc = current_context_id(&ctx);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> g(mu);
+    auto it = addr.find(ctx);
+    if (it == addr.end()) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_stream_status);
+        if (e != cudaSuccess || !p)
+            return e == cudaErrorMemoryAllocation ? NQ_ENOMEM : NQ_ECUDA;
+        it = addr.emplace(ctx, static_cast<int *>(p)).first;
+    }
+    *out = it->second;
+    return NQ_OK;
+}
+
+int stream_status(cudaStream_t s, int **out) {
+    static std::mutex mu;
+    // (context id, stream handle) -> word index; index 0 is the shared overflow word
+    static std::map<std::pair<unsigned long long, uintptr_t>, int> slot;
+    static std::unordered_map<unsigned long long, int> next;
+    int *words = nullptr;
+    int rc = stream_status_words(&words);
+    if (rc) return rc;
+    unsigned long long ctx = 0;
+    if ((rc = current_context_id(&ctx))) return rc;
+    std::lock_guard<std::mutex> g(mu);
+    const auto key = std::make_pair(ctx, reinterpret_cast<uintptr_t>(s));
+    auto it = slot.find(key);
+    if (it == slot.end()) {
+        int &n = next[ctx];
+        if (n == 0) n = 1;
+        it = slot.emplace(key, n < kStatusWords ? n++ : 0).first;
+    }
+    *out = words + it->second;
+    return NQ_OK;
+}
+
+int take_status(int *d_status, cudaStream_t s) {
+    if (!d_status) return NQ_OK;
     int v = 0;
-    const int zero = 0;
-    if (cudaMemcpyFromSymbol(&v, g_status, sizeof(int)) != cudaSuccess) return NQ_ECUDA;
-    if (v != 0 && cudaMemcpyToSymbol(g_status, &zero, sizeof(int)) != cudaSuccess)
+    if (cudaMemcpyAsync(&v, d_status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return NQ_ECUDA;
+    if (v != 0 && (cudaMemsetAsync(d_status, 0, sizeof(int), s) != cudaSuccess ||
+                   cudaStreamSynchronize(s) != cudaSuccess))
         return NQ_ECUDA;
     return v;
 }

@@ -8,8 +8,12 @@
 // never reads host memory to claim). The persistent kernel picks the new
 // subproblems up while it is still searching older ones. Admission: a request
 // is taken only when a slot is free, the ring has room (ring positions are
-// reused only below the end of the latest completed request: claims are in
-// ring order, so everything below it has been read), and its stack footprint
+// reused only below the end of the longest run of completed requests in
+// submission order: a request completes only after every one of its records
+// was loaded and searched, and requests occupy the ring in submission order,
+// so every record below that end has been read -- a later request that
+// completes early does not move it, since a lane may still hold a claimed but
+// unread index of an earlier one), and its stack footprint
 // fits the running kernel's (its prefix depth is raised until N - 1 - d frames
 // fit, and further while it has fewer than four subproblems per resident lane).
 #include <algorithm>
@@ -17,6 +21,7 @@
 #include <deque>
 #include <mutex>
 #include <new>
+#include <unordered_set>
 #include <vector>
 
 #include "nq_internal.h"
@@ -27,10 +32,12 @@ using nqi::ServeSlot;
 
 // Device control words, each on its own 128-byte line: the claim cursor at
 // [0] and the head mirror at [kHeadWord] (u64 units), then the idle-exit
-// counters (u32, reset before every launch) from byte kExitBytes on.
-constexpr size_t kCtlBytes = 640;
+// counters (u32, reset before every launch) from byte kExitBytes to
+// kStatusByte, then the server's error word (read and cleared by polls).
+constexpr size_t kCtlBytes = 768;
 constexpr size_t kHeadWord = 16;
 constexpr size_t kExitBytes = 256;
+constexpr size_t kStatusByte = 640;
 
 struct nq_server {
     nq_server_config cfg{};
@@ -49,7 +56,7 @@ struct nq_server {
     ServeControl *h_ctl = nullptr, *d_ctl = nullptr;
     ServeDone *h_done = nullptr, *d_done = nullptr;
     uint64_t head = 0;       // records published
-    uint64_t consumed = 0;   // every index below has been claimed
+    uint64_t consumed = 0;   // every record below has been loaded by the kernel
     uint64_t next_ticket = 1;
     uint64_t launches = 0, submitted = 0, completed = 0;
     struct Req {
@@ -59,7 +66,12 @@ struct nq_server {
     std::vector<Req> req;
     std::vector<uint32_t> gen;
     std::deque<std::pair<uint64_t, uint64_t>> ready;
+    // requests holding ring records, in submission order: (ticket, ring end)
+    std::deque<std::pair<uint64_t, uint64_t>> in_ring;
+    std::unordered_set<uint64_t> done_early;  // completed, not yet at the front
     std::mutex mu;
+    int *status() { return reinterpret_cast<int *>(reinterpret_cast<unsigned char *>(d_cursor) +
+                                                   kStatusByte); }
 };
 
 namespace {
@@ -99,8 +111,9 @@ int ensure_running(nq_server *s) {
     a.idle_warps = reinterpret_cast<unsigned int *>(exitw);
     a.started_warps = reinterpret_cast<unsigned int *>(exitw + 128);
     a.closing = reinterpret_cast<unsigned int *>(exitw + 256);
-    if (cudaMemsetAsync(exitw, 0, kCtlBytes - kExitBytes, s->kstream) != cudaSuccess)
+    if (cudaMemsetAsync(exitw, 0, kStatusByte - kExitBytes, s->kstream) != cudaSuccess)
         return NQ_ECUDA;
+    a.status = s->status();
     a.ctl = s->d_ctl;
     a.slot_info = s->d_slot;
     a.slot_total = s->d_total;
@@ -131,9 +144,15 @@ void collect(nq_server *s) {
         if (s->h_done[i].seq != r.ticket) continue;
         std::atomic_thread_fence(std::memory_order_acquire);
         s->ready.emplace_back(r.ticket, (uint64_t)s->h_done[i].total);
-        s->consumed = std::max(s->consumed, r.end);
+        s->done_early.insert(r.ticket);
         r.active = false;
         ++s->completed;
+    }
+    // the ring watermark: the end of the longest completed run from the front
+    while (!s->in_ring.empty() && s->done_early.count(s->in_ring.front().first)) {
+        s->consumed = s->in_ring.front().second;
+        s->done_early.erase(s->in_ring.front().first);
+        s->in_ring.pop_front();
     }
 }
 
@@ -311,6 +330,7 @@ extern "C" int nq_server_submit(nq_server *s, int N, const nq_queen *q, int k, u
     s->req[slot].ticket = tk;
     s->req[slot].end = s->head;
     s->req[slot].active = true;
+    s->in_ring.emplace_back(tk, s->head);
     s->next_ticket++;
     ++s->submitted;
     *ticket = tk;
@@ -328,11 +348,14 @@ extern "C" int nq_server_poll(nq_server *s, uint64_t *tickets, uint64_t *counts,
     if (s->launched) {
         const cudaError_t q = cudaEventQuery(s->kdone);
         if (q != cudaSuccess && q != cudaErrorNotReady) return NQ_ECUDA;
-        // the kernel left (idle) while work was being published: start it again
-        if (q == cudaSuccess && pending) rc = ensure_running(s);
         if (q == cudaSuccess) {
-            const int st = nqi::take_device_status();
-            if (st && !rc) rc = st;
+            // the kernel has left: its error word is final (read before any relaunch)
+            rc = nqi::take_status(s->status(), s->cstream);
+            // it left (idle) while work was being published: start it again
+            if (pending) {
+                const int lrc = ensure_running(s);
+                if (!rc) rc = lrc;
+            }
         }
     }
     int n = 0;

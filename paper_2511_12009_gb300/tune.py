@@ -6,8 +6,9 @@ the kernel's own CUDA events inside nq_total_ex (best of `reps`); every
 candidate must return the same total. The search is staged (depth, then
 layout, then block and order, then chunk), each stage keeping the best of the
 previous ones, so a board size costs a few dozen launches. Results are cached
-in a JSON file keyed by device name, SM count and board size
-(``NQ_TUNE_CACHE``, default ``paper_2511_12009_gb300/_build/tune_cache.json``).
+in a JSON file keyed by device name, SM count, a hash of libnq's sources (a
+kernel change invalidates every entry) and board size (``NQ_TUNE_CACHE``,
+default ``paper_2511_12009_gb300/_build/tune_cache.json``).
 """
 from __future__ import annotations
 
@@ -23,10 +24,22 @@ _lock = threading.Lock()
 FIELDS = ("layout", "block", "blocks_per_sm", "order", "d", "claim")
 
 
+def _source_hash() -> str:
+    """sha256 (first 16 hex digits) over libnq's sources and headers."""
+    import hashlib
+    from . import _build
+    h = hashlib.sha256()
+    for path in sorted(_build._inputs()):
+        h.update(os.path.basename(path).encode())
+        with open(path, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def _device_key() -> str:
     import torch
     p = torch.cuda.get_device_properties(torch.cuda.current_device())
-    return f"{p.name}|{p.multi_processor_count}"
+    return f"{p.name}|{p.multi_processor_count}|{_source_hash()}"
 
 
 def _load() -> dict:

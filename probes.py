@@ -1,7 +1,7 @@
 """Command-line driver of the measurement probes (include/nq.h, "Measurement").
 
-    python -m paper_2511_12009_gb300.probes alu     # integer issue rates (the roofline)
-    python -m paper_2511_12009_gb300.probes smem    # shared-memory access patterns
+    python probes.py alu     # integer issue rates (the roofline)
+    python probes.py smem    # shared-memory access patterns
 
 ``smem`` runs one launch per pattern, in the order of CASES, and prints one JSON
 line per launch with what a conflict-free access pattern needs: for each warp
@@ -18,7 +18,7 @@ import json
 import math
 import sys
 
-from . import nq
+from paper_2511_12009_gb300 import nq
 
 # (kind, lane mask, density out of 32, what it is)
 CASES = [

@@ -101,12 +101,31 @@ def test_enumerate_rejects_bad_sizes(args):
     assert nq.lib().nq_enumerate_prefixes(args[0], args[1], None, 0, ctypes.byref(num)) == nq.NQ_EINVAL
 
 
-def test_enumerate_cap_overflow():
+def test_enumerate_cap_too_small():
+    """A buffer smaller than the set: NQ_EINVAL, the set's size in *n_out, nothing written."""
     out = np.zeros(3, dtype=nq.PREFIX_DTYPE)
     num = ctypes.c_uint64(0)
     rc = nq.lib().nq_enumerate_prefixes(8, 3, out.ctypes.data, 3, ctypes.byref(num))
-    assert rc == nq.NQ_EOVERFLOW and num.value == nq.prefix_count(8, 3)
-    assert np.array_equal(out, nq.enumerate_prefixes(8, 3)[:3])
+    assert rc == nq.NQ_EINVAL and num.value == nq.prefix_count(8, 3)
+    assert not out.view(np.uint32).any()
+    parent = nq.enumerate_prefixes(9, 2)[0]
+    kids = nq.descendants(parent, 2)
+    par = np.ascontiguousarray(np.asarray(parent, dtype=nq.PREFIX_DTYPE).reshape(1))
+    small = np.zeros(len(kids) - 1, dtype=nq.PREFIX_DTYPE)
+    rc = nq.lib().nq_descendants(par.ctypes.data, 2, small.ctypes.data, len(small),
+                                 ctypes.byref(num))
+    assert rc == nq.NQ_EINVAL and num.value == len(kids) and not small.view(np.uint32).any()
+
+
+@pytest.mark.parametrize("n", [20, 21, 22])
+def test_sampled_ranks_equal_oracle_golden(n):
+    """The library's unranking at the benchmark depth equals the oracle's prefixes
+    stored with the seeded N=20..22 samples (tests/golden/make_golden.py)."""
+    g = np.load(os.path.join(GOLDEN, f"oracle_n{n}_d7_s2048.npz"))
+    got = nq.prefixes_at_ranks(n, 7, g["ranks"])
+    assert np.array_equal(got["meta"] & 3, g["weights"])
+    for rec, q in zip(got, g["cols"]):
+        assert (int(rec["cols"]), int(rec["ld"]), int(rec["rd"])) == to_state(n, q)
 
 
 def test_total_rejects_overflowing_sizes():

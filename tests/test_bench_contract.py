@@ -35,3 +35,24 @@ def test_reference_arm_other_ranks_print_nothing():
     lines = run_bench(["--impl", "reference", "--steps", "1", "--warmup", "0", "--n", "12"],
                       {"WORLD_SIZE": "2", "RANK": "1", "LOCAL_RANK": "1"})
     assert lines == []
+
+
+def test_reference_arm_depth_matches_the_library():
+    """The reference arm restates the library's default depth instead of loading
+    libnq; the two rules agree for every board size."""
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2511_12009_gb300 import nq
+    for n in range(1, 32):
+        assert bench.default_depth(n) == nq.default_depth(n), n
+
+
+def test_reference_arm_does_not_load_the_library():
+    code = ("import sys, runpy; sys.argv = ['bench.py', '--impl', 'reference', '--steps', '1', "
+            "'--warmup', '0', '--n', '10']; runpy.run_path('bench.py', run_name='__main__'); "
+            "print('LOADED' if any(m.startswith('paper_2511_12009_gb300') for m in sys.modules) "
+            "else 'CLEAN')")
+    r = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True,
+                       timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert r.stdout.strip().splitlines()[-1] == "CLEAN"

@@ -3,7 +3,8 @@ issue-rate probe (the roofline's denominator) and the shared-memory pattern
 probe (whose launches the bank-counter profile reads)."""
 import pytest
 
-from paper_2511_12009_gb300 import nq, probes
+import probes
+from paper_2511_12009_gb300 import nq
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")

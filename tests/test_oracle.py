@@ -252,3 +252,25 @@ def test_descendants_by_brute_force(orc, n, base, rows):
     want = [tuple(base) + t for t in itertools.product(range(n), repeat=rows)
             if _nonattacking(tuple(base) + t)]
     assert orc.descendants(n, base, rows) == want
+
+
+@pytest.mark.parametrize("n,fname", [(20, "oracle_n20_d7_s2048.npz"), (21, "oracle_n21_d7_s2048.npz"),
+                                     (22, "oracle_n22_d7_s2048.npz")])
+def test_sampled_goldens_follow_their_recipe(orc, n, fname):
+    """The stored N=20..22 samples are what their recipe says: the seeded ranks
+    (SplitMix64 draws over the oracle's set size), the oracle's own prefixes at
+    those ranks, every weight 2 (d >= 2), and -- re-derived here for the first
+    entries, whole-board brute force being out of reach -- the oracle's counts;
+    every count is at most the entry's node count (each solution is a node)."""
+    g = np.load(os.path.join(os.path.dirname(__file__), "golden", fname))
+    size = orc.prefix_count(n, 7)
+    assert int(g["set_size"][0]) == size
+    ranks = synth_inputs.sample_ranks(int(g["seed"][0]), size, len(g["ranks"]))
+    assert np.array_equal(g["ranks"], np.array(ranks, dtype=np.uint64))
+    head = orc.prefixes_at_ranks(n, 7, g["ranks"][:64])
+    assert np.array_equal(g["cols"][:64], head)
+    assert (g["weights"] == 2).all()
+    k = 4 if n < 22 else 2
+    c, v = orc.count_prefixes(n, g["cols"][:k])
+    assert np.array_equal(c, g["counts"][:k]) and np.array_equal(v, g["nodes"][:k])
+    assert (g["counts"] <= g["nodes"]).all()

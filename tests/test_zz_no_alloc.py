@@ -7,8 +7,11 @@ The entry point keeps its device side in one static array inside libnq. This
 test calls it through the C ABI with host arrays and checks its counts and
 total against nq_count on the same prefixes -- exact equality, as every count
 is an integer -- on two calls in a row (so the second call sees the first
-one's leftovers in the shared array), and checks that a batch larger than the
-array is refused. The file is named so that pytest collects it last.
+one's leftovers in the shared array); checks every per-prefix count of the
+N=16 depth-5 set against the CPU oracle's stored arrays; checks that the
+device's free memory is the same before and after calls (nothing allocated);
+and checks that a batch larger than the array is refused. The file is named
+so that pytest collects it last.
 """
 import ctypes
 import json
@@ -76,3 +79,29 @@ def test_batch_beyond_the_array_is_refused():
     assert len(pre) > MAX_PREFIXES
     rc, _, total = noalloc(18, 6, pre)
     assert rc == nq.NQ_EOVERFLOW and total == 12345
+
+
+def test_counts_equal_the_oracle_arrays():
+    """N=16, d=5: all 70,906 per-prefix counts against the oracle's stored arrays."""
+    import numpy as np
+    g = np.load(os.path.join(GOLDEN, "oracle_n16_d5.npz"))
+    pre = nq.enumerate_prefixes(16, 5)
+    rc, got, total = noalloc(16, 5, pre)
+    assert rc == nq.NQ_OK, nq.strerror(rc)
+    assert np.array_equal(got, g["counts"]) and total == Q[16]
+
+
+def test_calls_allocate_no_device_memory():
+    """After a first call (which commits the static array), further calls leave
+    the device's free memory exactly where it was."""
+    pre = nq.enumerate_prefixes(15, 4)
+    assert noalloc(15, 4, pre[:0])[0] == nq.NQ_OK     # n = 0: set-up only
+    assert noalloc(15, 4, pre)[0] == nq.NQ_OK         # the kernel's first launch
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(3):
+        rc, _, total = noalloc(15, 4, pre)
+        assert rc == nq.NQ_OK and total == Q[15]
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
