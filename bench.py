@@ -74,8 +74,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=18)
     ap.add_argument("--d", type=int, default=0, help="prefix depth (0 = library default)")
-    ap.add_argument("--layout", default="default", choices=["default", "paper", "reg", "wt", "wt32", "wt32a", "wtm",
-                                                      "regm"])
+    ap.add_argument("--layout", default="default",
+                    choices=["default", "paper", "reg", "wt", "wt32", "wt32a", "wtm", "regm",
+                             "regp", "regz", "regpz"])
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--bps", type=int, default=0, help="blocks per SM (0 = max)")
     ap.add_argument("--order", type=int, default=0, help="0 default, 1 index order, 2 reverse")

@@ -104,11 +104,21 @@ typedef struct nq_queen {
                              (issuable on the FMA pipe as well as the ALU pipe) */
 #define NQ_LAYOUT_WTM 6   /* WT with the step's disjoint-bit arithmetic written as
                              integer multiply-adds, balancing the FMA and ALU pipes */
-#define NQ_LAYOUT_REGM 7  /* REG with the same multiply-add arithmetic */
+#define NQ_LAYOUT_REGM 7  /* REG with the same multiply-add arithmetic, the control tail as
+                             one predicated block (the default) */
+#define NQ_LAYOUT_REGP 8  /* REGM without the last-row rule: the row N-1 child is pushed and
+                             a solution is the step that fills every column (one compare
+                             instead of a population count; one more frame per thread) */
+#define NQ_LAYOUT_REGZ 9  /* REGM with each frame saved and restored as four 32-bit words
+                             in four arrays, every word in its lane's own bank: zero bank
+                             conflicts for any set of active lanes (256-thread blocks) */
+#define NQ_LAYOUT_REGPZ 10 /* REGP with REGZ's split-word frames */
+#define NQ_LAYOUT_LAST NQ_LAYOUT_REGPZ
 
 /* Launch configuration. Zero in any field selects the default: for layout,
  * block, claim and d the environment variables NQ_LAYOUT (a layout number or
- * name: paper, reg, wt, wt32, wt32a, wtm, regm), NQ_BLOCK, NQ_CLAIM and NQ_D
+ * name: paper, reg, wt, wt32, wt32a, wtm, regm, regp, regz, regpz), NQ_BLOCK,
+ * NQ_CLAIM and NQ_D
  * when set to a valid value, else the library's own default. (Batches take
  * their configuration as given.) */
 typedef struct nq_config {

@@ -42,11 +42,13 @@ int env_int(const char *name) {
 int env_layout() {
     const char *v = std::getenv("NQ_LAYOUT");
     if (!v || !*v) return 0;
-    static const char *names[] = {"default", "paper", "reg", "wt", "wt32", "wt32a", "wtm", "regm"};
-    for (int i = 0; i < 8; ++i)
+    static const char *names[] = {"default", "paper", "reg",  "wt",   "wt32",  "wt32a",
+                                  "wtm",     "regm",  "regp", "regz", "regpz"};
+    static_assert(sizeof(names) / sizeof(names[0]) == NQ_LAYOUT_LAST + 1, "one name per layout");
+    for (int i = 0; i <= NQ_LAYOUT_LAST; ++i)
         if (std::strcmp(v, names[i]) == 0) return i;
     const int x = env_int("NQ_LAYOUT");
-    return x <= NQ_LAYOUT_REGM ? x : 0;
+    return x <= NQ_LAYOUT_LAST ? x : 0;
 }
 
 // The configuration a call runs with: the caller's fields, and for the ones it
@@ -137,7 +139,7 @@ int enqueue_search(const nq_prefix *d_prefixes, uint64_t n, int expect_n, int mi
     int rc = make_plan(max_n, min_d, diag, constrained, cfg, &p, false, published != nullptr);
     if (rc) return rc;
     // Scratch: the work cursor, and with donation its counters and item ring.
-    const bool reg = p.layout == NQ_LAYOUT_REG || p.layout == NQ_LAYOUT_REGM;
+    const bool reg = p.layout == NQ_LAYOUT_REG || p.layout == NQ_LAYOUT_REGM;  // donation forms
     // Donation (its own kernel variant, planned again: its occupancy differs)
     // only when asked for: measured on GB300 it has not paid for its queue
     // traffic yet, so batches short of work are better split on the host
@@ -333,7 +335,7 @@ extern "C" int nq_total_ex(int N, const nq_config *cfg, uint64_t *total_out, uin
     // streamed input needs a register-stack layout (the default); any other
     // layout searches once every piece is in
     const int lay = cfg->layout ? cfg->layout : NQ_LAYOUT_REGM;
-    const bool stream_in = npieces > 1 && (lay == NQ_LAYOUT_REG || lay == NQ_LAYOUT_REGM);
+    const bool stream_in = npieces > 1 && layout_register_top(lay);
     cudaEventRecord(ev[0], ctx.s);
     rc = cuda_rc(cudaMemsetAsync(d_tot, 0, 32 * sizeof(uint64_t), ctx.s));
     if (!rc) rc = cuda_rc(cudaMemsetAsync(d_ctl, 0, 256, ctx.s));

@@ -92,6 +92,30 @@ __host__ __device__ constexpr uint32_t stack_array_bytes(uint32_t block, uint32_
                                                          uint32_t elem) {
     return slots * block * elem;
 }
+// Split-word frames (layouts REGZ and REGPZ): word `field` of slot k of
+// thread t at ((4k + field) * block + t) * 4 -- a frame's four words are
+// block * 4 bytes apart and every word of thread t is in bank t mod 32, so
+// any set of lanes reads or writes one word each in a single wavefront.
+// Whole-frame layouts: (k * block + t) * 16 + 4 * field.
+__host__ __device__ constexpr uint32_t stack_word_offset(bool split, uint32_t block,
+                                                         uint32_t thread, uint32_t slot,
+                                                         uint32_t field) {
+    return split ? ((4u * slot + field) * block + thread) * 4u
+                 : stack_slot_offset(block, thread, slot, 16u) + 4u * field;
+}
+// The split-word kernels are built for this block size (their word stride is
+// an immediate offset).
+constexpr uint32_t kZBlock = 256;
+__host__ __device__ constexpr bool layout_split_words(int layout) {
+    return layout == NQ_LAYOUT_REGZ || layout == NQ_LAYOUT_REGPZ;
+}
+__host__ __device__ constexpr bool layout_regm_family(int layout) {
+    return layout == NQ_LAYOUT_REGM || layout == NQ_LAYOUT_REGP || layout == NQ_LAYOUT_REGZ ||
+           layout == NQ_LAYOUT_REGPZ;
+}
+__host__ __device__ constexpr bool layout_register_top(int layout) {
+    return layout == NQ_LAYOUT_REG || layout_regm_family(layout);
+}
 
 // Constrained mode packs the row index of a frame into bits 27..31 of cols.
 constexpr int kRowShift = 27;

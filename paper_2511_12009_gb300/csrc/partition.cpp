@@ -34,10 +34,16 @@ extern "C" int nq_partition(uint64_t n, const float *ratios, int k, uint64_t *fi
 extern "C" int nq_stack_offset(int layout, int block, int slots, int thread, int slot, int field,
                                uint32_t *offset_out) {
     if (layout == NQ_LAYOUT_DEFAULT) layout = NQ_LAYOUT_REGM;
-    if (layout < NQ_LAYOUT_PAPER || layout > NQ_LAYOUT_REGM || block < 32 || block > 1024 ||
+    if (layout < NQ_LAYOUT_PAPER || layout > NQ_LAYOUT_LAST || block < 32 || block > 1024 ||
         block % 32 || slots < 1 || slots > 64 || thread < 0 || thread >= block || slot < 0 ||
         slot >= slots || field < 0 || field > 3 || !offset_out)
         return NQ_EINVAL;
+    if (nqi::layout_split_words(layout)) {  // REGZ / REGPZ: four word arrays per slot
+        if (block != (int)nqi::kZBlock) return NQ_EINVAL;
+        *offset_out = nqi::stack_word_offset(true, (uint32_t)block, (uint32_t)thread,
+                                             (uint32_t)slot, (uint32_t)field);
+        return NQ_OK;
+    }
     const bool split = layout == NQ_LAYOUT_WT32 || layout == NQ_LAYOUT_WT32A;
     const uint32_t elem = nqi::stack_elem_bytes(split);
     const uint32_t at = nqi::stack_slot_offset((uint32_t)block, (uint32_t)thread, (uint32_t)slot, elem);

@@ -59,9 +59,11 @@ constexpr int kChunk = 15;
 static_assert(kChunk < 16, "the sentinel frame holds 16 idle steps (32 for ~0 masks)");
 constexpr uint32_t kRowInc = 1u << kRowShift;
 // Constrained-mode sentinel: row field 30, so the child is row 31 whose allowed
-// mask is 0 -- no push, no count; its candidate bits stay below the row field,
-// so cols never wraps.
-constexpr uint32_t kSentinelC = (30u << kRowShift) | (kRowInc - 1u);
+// mask is 0 -- no push, no count. Its 27 candidate bits lie below the row field
+// and in none of its masks (cols, ld and rd hold no column), so the sums of the
+// multiply-add form stay exact and cols never wraps: 27 idle steps per frame.
+constexpr uint32_t kSentinelC = 30u << kRowShift;
+constexpr uint32_t kSentinelLrC = 0u;
 constexpr uint32_t kSentinelAvC = kRowInc - 1u;
 static_assert(kChunk < kRowShift, "constrained sentinel holds 27 idle steps");
 
@@ -121,6 +123,30 @@ __device__ __forceinline__ void stcg4(void *p, uint4 v) {
                  : "memory");
 }
 
+// Split-word frames (layouts REGZ, REGPZ): word j of a frame lies kZWord * j
+// bytes above word 0, so that every stack access is one 32-bit word in the
+// lane's own bank (stack_word_offset). The word stride is a compile-time
+// constant (blocks of kZBlock threads) so that the four accesses of a frame
+// share one address register with immediate offsets.
+constexpr uint32_t kZWord = 4u * kZBlock;
+template <bool SPLIT>
+__device__ __forceinline__ void frame_store(uint32_t a, uint4 v) {
+    if (SPLIT) {
+        sts1(a, v.x);
+        sts1(a + kZWord, v.y);
+        sts1(a + 2u * kZWord, v.z);
+        sts1(a + 3u * kZWord, v.w);
+    } else {
+        sts4(a, v);
+    }
+}
+template <bool SPLIT>
+__device__ __forceinline__ uint4 frame_load(uint32_t a) {
+    if (SPLIT) return make_uint4(lds1(a), lds1(a + kZWord), lds1(a + 2u * kZWord),
+                                 lds1(a + 3u * kZWord));
+    return lds4(a);
+}
+
 constexpr unsigned kReadySpins = 1u << 20;   // wait for a reserved item to be written
 constexpr int kMinDonateRows = 11;  // donate only frames with >= 11 rows below (~1e4+ nodes)
 constexpr unsigned kMaxIdleRounds = 1u << 21;  // polls (<= 64 us apart): gives up after ~2 min
@@ -146,7 +172,11 @@ struct Lane {
 //
 // MADD (layout REGM): the disjoint-bit arithmetic as integer multiply-adds by
 // run-time multipliers, as in step_wtm, so it issues on the FMA pipe.
-template <bool DIAG, bool CONSTR, bool MADD = false>
+// PUSHLAST (layouts REGP, REGPZ): no last-row rule; the row N-1 child is
+// pushed like any other and a solution is the step that fills every column
+// (cols == ~0 with the columns >= N pre-set). SPLIT: split-word frames.
+// (The diagnostic builds of REGM, REGP, REGZ and REGPZ run this form.)
+template <bool DIAG, bool CONSTR, bool MADD = false, bool PUSHLAST = false, bool SPLIT = false>
 __device__ __forceinline__ void step_reg(uint32_t &c, uint32_t &l, uint32_t &r, uint32_t &av,
                                          uint32_t &top, const Lane &k, uint32_t &s32,
                                          uint32_t &n32, const uint32_t m1 = 1u,
@@ -167,21 +197,24 @@ __device__ __forceinline__ void step_reg(uint32_t &c, uint32_t &l, uint32_t &r, 
     uint32_t c2, a2;
     bool lastrow;
     if (CONSTR) {
-        c2 = (c | p) + kRowInc;
+        c2 = (MADD ? p * m1 + c : (c | p)) + kRowInc;
         a2 = ~(c2 | l2 | r2) & lds1(k.table + ((c2 >> kRowShift) << 2));
         lastrow = c2 >= k.thr;
     } else {
         c2 = MADD ? p * m1 + c : c | p;
         a2 = ~(c2 | l2 | r2);  // free columns of the next row
-        lastrow = one_free(c2);
+        lastrow = PUSHLAST ? false : one_free(c2);
     }
     const bool live = a2 != 0u;
-    s32 += (lastrow && live) ? 1u : 0u;  // Algorithm 3: count instead of pushing
+    if (PUSHLAST)
+        s32 += (c2 == ~0u) ? 1u : 0u;  // every column holds a queen: a solution
+    else
+        s32 += (lastrow && live) ? 1u : 0u;  // Algorithm 3: count instead of pushing
     if (DIAG) n32 += (top != k.base) ? 1u : 0u;  // top == base: idle on the sentinel
     const bool push = !lastrow && live;
     if (push && ar != 0u) {
         if (!DIAG || top < k.limit) {
-            sts4(top, make_uint4(c, l, r, ar));
+            frame_store<SPLIT>(top, make_uint4(c, l, r, ar));
             top += k.stride;
         } else {
             record_error(k.status, NQ_ESTACK);
@@ -190,12 +223,12 @@ __device__ __forceinline__ void step_reg(uint32_t &c, uint32_t &l, uint32_t &r, 
     if (!push && ar == 0u) {
         if (!DIAG || top > k.base) {
             top -= k.stride;
-            const uint4 f = lds4(top);
+            const uint4 f = frame_load<SPLIT>(top);
             c = f.x; l = f.y; r = f.z; av = f.w;
         } else {
             record_error(k.status, NQ_ESTACK);
             c = CONSTR ? kSentinelC : MADD ? 0xAAAAAAAAu : ~0u;
-            l = r = MADD ? 0xAAAAAAAAu : ~0u;
+            l = r = CONSTR ? kSentinelLrC : MADD ? 0xAAAAAAAAu : ~0u;
             av = CONSTR ? kSentinelAvC : MADD ? 0x55555555u : ~0u;
         }
     } else if (push) {
@@ -211,42 +244,121 @@ __device__ __forceinline__ void step_reg(uint32_t &c, uint32_t &l, uint32_t &r, 
 // that every lane executes the same straight-line code (no divergent branch
 // around the push / pop cases). p is the chosen column, ar the candidates
 // left here, (c2, l2, r2, a2) the child. Operands: %0..%5 = c, l, r, av, top,
-// s32 (updated); %6..%12 = popc(c2), a2, ar, c2, l2, r2, stride.
+// s32 (updated); %6..%12 = popc(c2) (unused with PUSHLAST), a2, ar, c2, l2,
+// r2, stride.
+//
+// PUSHLAST (layouts REGP, REGPZ): Algorithm 2 without Algorithm 3's last-row
+// rule: the row N-1 child is pushed like any other, and the step that places
+// the last queen is recognised by cols == ~0 (the columns >= N are pre-set),
+// one compare instead of a population count and two predicates. It costs one
+// more step per solution (about 1 % of the steps at N = 18..22) and one more
+// stack frame (rows d..N-2 may be saved).
+// SPLIT (layouts REGZ, REGPZ): the frame is saved and restored as four 32-bit
+// words kZWord bytes apart, each in the lane's own bank.
+#define NQ_SAVE4 \
+    "@psave st.shared.v4.u32 [%4], {%0, %1, %2, %8};\n\t"
+#define NQ_LOAD4 \
+    "@ppop ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];\n\t"
+#define NQ_SAVEZ \
+    "@psave st.shared.u32 [%4], %0;\n\t"          \
+    "@psave st.shared.u32 [%4+1024], %1;\n\t"     \
+    "@psave st.shared.u32 [%4+2048], %2;\n\t"     \
+    "@psave st.shared.u32 [%4+3072], %8;\n\t"
+#define NQ_LOADZ \
+    "@ppop ld.shared.u32 %0, [%4];\n\t"           \
+    "@ppop ld.shared.u32 %1, [%4+1024];\n\t"      \
+    "@ppop ld.shared.u32 %2, [%4+2048];\n\t"      \
+    "@ppop ld.shared.u32 %3, [%4+3072];\n\t"
+#define NQ_PRED_LASTROW \
+    "setp.eq.u32 plast, %6, 31;\n\t"            /* queens in rows 0..N-2 (Algorithm 3) */ \
+    "setp.ne.and.u32 pcnt, %7, 0, plast;\n\t"   /* ... and row N-1 has its column free */ \
+    "setp.ne.and.u32 ppush, %7, 0, !plast;\n\t" /* a live child above the last row */
+#define NQ_PRED_ROWFIELD \
+    "setp.ge.u32 plast, %9, %6;\n\t"            /* the child is in row N-1 */ \
+    "setp.ne.and.u32 pcnt, %7, 0, plast;\n\t"   /* ... and takes a free, allowed column */ \
+    "setp.ne.and.u32 ppush, %7, 0, !plast;\n\t" /* a live child above the last row */
+#define NQ_PRED_PUSHLAST \
+    "setp.eq.u32 pcnt, %9, 0xFFFFFFFF;\n\t"     /* every column holds a queen */ \
+    "setp.ne.u32 ppush, %7, 0;\n\t"             /* a live child */
+#define NQ_TAIL(PRED, SAVE, LOAD) \
+    "{\n\t"                                                                         \
+    ".reg .pred plast, pcnt, ppush, psave, ppop;\n\t"                               \
+    PRED                                                                            \
+    "@pcnt add.u32 %5, %5, 1;\n\t"                                                  \
+    "setp.ne.and.u32 psave, %8, 0, ppush;\n\t"  /* keep this frame: columns left */  \
+    "setp.eq.and.u32 ppop, %8, 0, !ppush;\n\t"  /* exhausted, nothing pushed: pop */ \
+    SAVE                                                                            \
+    "@psave add.u32 %4, %4, %12;\n\t"                                               \
+    "@ppop sub.u32 %4, %4, %12;\n\t"                                                \
+    "selp.b32 %3, %7, %8, ppush;\n\t"                                               \
+    "@ppush mov.b32 %0, %9;\n\t"                                                    \
+    "@ppush mov.b32 %1, %10;\n\t"                                                   \
+    "@ppush mov.b32 %2, %11;\n\t"                                                   \
+    LOAD                                                                            \
+    "}"
+
+template <bool PUSHLAST, bool SPLIT>
 __device__ __forceinline__ void step_regm(uint32_t &c, uint32_t &l, uint32_t &r, uint32_t &av,
                                           uint32_t &top, const uint32_t stride, uint32_t &s32,
                                           const uint32_t m1, const uint32_t m2,
                                           const uint32_t mneg, const uint32_t mhalf) {
+    static_assert(!SPLIT || kZWord == 1024u, "the PTX offsets assume 256-thread blocks");
     const uint32_t p = av & (av * mneg);
     const uint32_t ar = p * mneg + av;
     const uint32_t c2 = p * m1 + c;
     const uint32_t l2 = l * m2 + p * m2;
     const uint32_t r2 = __umulhi(p * m1 + r, mhalf);
     const uint32_t a2 = ~(c2 | l2 | r2);
-    const uint32_t pc = __popc(c2);
-    asm volatile(
-        "{\n\t"
-        ".reg .pred plast, pcnt, ppush, psave, ppop;\n\t"
-        "setp.eq.u32 plast, %6, 31;\n\t"            // queens in rows 0..N-2 (Algorithm 3)
-        "setp.ne.and.u32 pcnt, %7, 0, plast;\n\t"   // ... and row N-1 has its column free
-        "setp.ne.and.u32 ppush, %7, 0, !plast;\n\t" // a live child above the last row
-        "@pcnt add.u32 %5, %5, 1;\n\t"
-        "setp.ne.and.u32 psave, %8, 0, ppush;\n\t"  // keep this frame: it has columns left
-        "setp.eq.and.u32 ppop, %8, 0, !ppush;\n\t"  // exhausted, nothing pushed: pop
-        "@psave st.shared.v4.u32 [%4], {%0, %1, %2, %8};\n\t"
-        "@psave add.u32 %4, %4, %12;\n\t"
-        "@ppop sub.u32 %4, %4, %12;\n\t"
-        "selp.b32 %3, %7, %8, ppush;\n\t"
-        "@ppush mov.b32 %0, %9;\n\t"
-        "@ppush mov.b32 %1, %10;\n\t"
-        "@ppush mov.b32 %2, %11;\n\t"
-        "@ppop ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];\n\t"
-        "}"
-        : "+r"(c), "+r"(l), "+r"(r), "+r"(av), "+r"(top),
-          "+r"(s32)
-        : "r"(pc), "r"(a2), "r"(ar), "r"(c2), "r"(l2), "r"(r2),
-          "r"(stride)
-        : "memory");
+    const uint32_t pc = PUSHLAST ? 0u : (uint32_t)__popc(c2);
+#define NQ_OPERANDS                                                                        \
+    : "+r"(c), "+r"(l), "+r"(r), "+r"(av), "+r"(top), "+r"(s32)                            \
+    : "r"(pc), "r"(a2), "r"(ar), "r"(c2), "r"(l2), "r"(r2), "r"(stride)                    \
+    : "memory"
+    if constexpr (!PUSHLAST && !SPLIT)
+        asm volatile(NQ_TAIL(NQ_PRED_LASTROW, NQ_SAVE4, NQ_LOAD4) NQ_OPERANDS);
+    else if constexpr (PUSHLAST && !SPLIT)
+        asm volatile(NQ_TAIL(NQ_PRED_PUSHLAST, NQ_SAVE4, NQ_LOAD4) NQ_OPERANDS);
+    else if constexpr (!PUSHLAST && SPLIT)
+        asm volatile(NQ_TAIL(NQ_PRED_LASTROW, NQ_SAVEZ, NQ_LOADZ) NQ_OPERANDS);
+    else
+        asm volatile(NQ_TAIL(NQ_PRED_PUSHLAST, NQ_SAVEZ, NQ_LOADZ) NQ_OPERANDS);
+#undef NQ_OPERANDS
 }
+
+// One constrained step in the multiply-add form (partial-board queries: the
+// server's kernel and nq_count_constrained): the row index rides in bits
+// 27..31 of cols and is advanced with the placement, the child's row takes
+// only its allowed columns (a shared-memory table of 32 masks at `table`,
+// read at the start of the step: its address depends only on the parent's
+// row), and the child is in the last row when its row field reaches thr =
+// (N-1) << 27 -- one compare where the unconstrained step counts bits.
+// Operand %6 is thr; the rest as in step_regm.
+__device__ __forceinline__ void step_regm_constr(uint32_t &c, uint32_t &l, uint32_t &r,
+                                                 uint32_t &av, uint32_t &top,
+                                                 const uint32_t stride, const uint32_t table,
+                                                 const uint32_t thr, uint32_t &s32,
+                                                 const uint32_t m1, const uint32_t m2,
+                                                 const uint32_t mneg, const uint32_t mhalf) {
+    const uint32_t allowed = lds1(table + ((c >> kRowShift) << 2) + 4u);
+    const uint32_t p = av & (av * mneg);
+    const uint32_t ar = p * mneg + av;
+    const uint32_t c2 = p * m1 + c + kRowInc;
+    const uint32_t l2 = l * m2 + p * m2;
+    const uint32_t r2 = __umulhi(p * m1 + r, mhalf);
+    const uint32_t a2 = ~(c2 | l2 | r2) & allowed;
+    asm volatile(NQ_TAIL(NQ_PRED_ROWFIELD, NQ_SAVE4, NQ_LOAD4)
+                 : "+r"(c), "+r"(l), "+r"(r), "+r"(av), "+r"(top), "+r"(s32)
+                 : "r"(thr), "r"(a2), "r"(ar), "r"(c2), "r"(l2), "r"(r2), "r"(stride)
+                 : "memory");
+}
+#undef NQ_SAVE4
+#undef NQ_LOAD4
+#undef NQ_SAVEZ
+#undef NQ_LOADZ
+#undef NQ_PRED_LASTROW
+#undef NQ_PRED_PUSHLAST
+#undef NQ_PRED_ROWFIELD
+#undef NQ_TAIL
 
 // One step, layout WT (write-through): the top frame lives in registers AND in
 // its stack slot. The child is computed in place; when it is pushed it is
@@ -430,7 +542,12 @@ __device__ __forceinline__ void step_paper(uint32_t &top, const Lane &k, uint32_
 
 template <int LAYOUT, bool DIAG, bool CONSTR, bool DONATE, bool STREAM = false>
 __device__ __forceinline__ void search_body(const SearchArgs &a) {
-    constexpr bool kRegm = LAYOUT == NQ_LAYOUT_REGM;
+    // the multiply-add family: REGM, and its forms with the last row pushed
+    // (REGP), split-word frames (REGZ) or both (REGPZ)
+    constexpr bool kRegm = LAYOUT == NQ_LAYOUT_REGM || LAYOUT == NQ_LAYOUT_REGP ||
+                           LAYOUT == NQ_LAYOUT_REGZ || LAYOUT == NQ_LAYOUT_REGPZ;
+    constexpr bool kPushLast = LAYOUT == NQ_LAYOUT_REGP || LAYOUT == NQ_LAYOUT_REGPZ;
+    constexpr bool kSplit = LAYOUT == NQ_LAYOUT_REGZ || LAYOUT == NQ_LAYOUT_REGPZ;
     constexpr bool kReg = LAYOUT == NQ_LAYOUT_REG || kRegm;
     constexpr bool kWt = LAYOUT == NQ_LAYOUT_WT;
     constexpr bool kWt32 = LAYOUT == NQ_LAYOUT_WT32 || LAYOUT == NQ_LAYOUT_WT32A;
@@ -441,15 +558,27 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
     // 0 and 1: an idle lane then has 32 sentinel steps before it could pop below
     // its stack, so it runs 31 steps between bookkeeping points instead of 15
     // (half the bookkeeping per node; measured 2.2 % faster at N=18).
-    constexpr bool kTwo = kRegm && !DIAG && !DONATE && !CONSTR;
+    constexpr bool kTwo = kRegm && !DIAG && !DONATE;
     constexpr int kSteps = kTwo ? 31 : kChunk;
-    static_assert(kSteps < 32, "two 16-step sentinels hold 32 idle steps");
+    static_assert(kSteps < 32, "two 16-step sentinels hold 32 idle steps (54 constrained)");
     static_assert(kReg || !CONSTR, "constrained mode uses the REG layout");
+    static_assert(!(kPushLast || kSplit) || (!CONSTR && !DONATE),
+                  "REGP / REGZ / REGPZ: plain and streamed search only");
     constexpr uint32_t kElem = stack_elem_bytes(kWt32);  // bytes of one slot in one array
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(nq_smem);
     Lane k;
-    k.stride = stack_slot_offset(blockDim.x, 0u, 1u, kElem);
-    k.base = sbase + stack_slot_offset(blockDim.x, threadIdx.x, 0u, kElem);
+    if (kSplit) {
+        // split-word frames: the word stride is compiled in (kZBlock threads)
+        if (blockDim.x != kZBlock) {
+            record_error(a.status, NQ_EINVAL);
+            return;
+        }
+        k.stride = stack_word_offset(true, kZBlock, 0u, 1u, 0u);
+        k.base = sbase + stack_word_offset(true, kZBlock, threadIdx.x, 0u, 0u);
+    } else {
+        k.stride = stack_slot_offset(blockDim.x, 0u, 1u, kElem);
+        k.base = sbase + stack_slot_offset(blockDim.x, threadIdx.x, 0u, kElem);
+    }
     k.limit = k.base + (uint32_t)a.slots * k.stride;
     // WT32: bytes per array; constrained mode: address of allowed[] after the stacks
     const uint32_t arr = stack_array_bytes(blockDim.x, (uint32_t)a.slots, kElem);
@@ -464,7 +593,7 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
         __syncthreads();
     }
     const uint32_t sent_c = CONSTR ? kSentinelC : kArith ? 0xAAAAAAAAu : ~0u;
-    const uint32_t sent_lr = kArith ? 0xAAAAAAAAu : ~0u;
+    const uint32_t sent_lr = CONSTR ? kSentinelLrC : kArith ? 0xAAAAAAAAu : ~0u;
     const uint32_t sent_av = CONSTR ? kSentinelAvC : kArith ? 0x55555555u : ~0u;
 
     uint32_t c = sent_c, l = sent_lr, r = sent_lr, av = sent_av;  // the top frame
@@ -478,8 +607,9 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
         sts1(k.base + 2u * k.table, sent_lr);
         sts1(k.base + 3u * k.table, sent_av);
     } else {
-        sts4(k.base, make_uint4(sent_c, sent_lr, sent_lr, sent_av));
-        if (kTwo) sts4(k.base + k.stride, make_uint4(sent_c, sent_lr, sent_lr, sent_av));
+        frame_store<kSplit>(k.base, make_uint4(sent_c, sent_lr, sent_lr, sent_av));
+        if (kTwo)
+            frame_store<kSplit>(k.base + k.stride, make_uint4(sent_c, sent_lr, sent_lr, sent_av));
     }
     if (!kRegs) top = k.base + k.stride;
     const uint32_t idle_top = kRegs ? k.base : k.base + k.stride;
@@ -544,7 +674,10 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
         const bool idle = kTwo ? top <= k.base + k.stride : top == idle_top;
         if (idle) {
             if (idx != kNone) {
-                finish(idx, sol, nod + sol, wt, pn);
+                // nodes: the steps taken, plus the last-row placements Algorithm
+                // 3 counts without a step (with the last row pushed, solutions
+                // are steps)
+                finish(idx, sol, kPushLast ? nod : nod + sol, wt, pn);
                 idx = kNone;
             }
             if (kRegs) {
@@ -604,10 +737,11 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
                                     (w == 1u || w == 2u) && d <= n && (P.x & ~last) == 0u &&
                                     (uint32_t)__popc(P.x) == d &&
                                     (!CONSTR || n <= (uint32_t)kMaxConstrainedN);
-                    const int need_slots = kReg ? (int)n - 1 - (int)d + (kTwo ? 1 : 0)
-                                                : (int)n - (int)d;
-                    // (REG: sentinel + ancestors of rows d..N-3; WT / PAPER: sentinel +
-                    // frames of rows d..N-2)
+                    const int need_slots =
+                        kReg ? (int)n - 2 - (int)d + (kPushLast ? 1 : 0) + (kTwo ? 2 : 1)
+                             : (int)n - (int)d;
+                    // (REG: sentinel(s) + ancestors of rows d..N-3, or d..N-2 with the
+                    // last row pushed; WT / PAPER: sentinel + frames of rows d..N-2)
                     if (!ok) {
                         record_error(k.status, NQ_EINVAL);
                         finish(pi, 0, 0, 0, 0);
@@ -841,10 +975,17 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
         uint32_t s32 = 0, n32 = 0;
 #pragma unroll
         for (int j = 0; j < kSteps; ++j) {
-            if (kRegm && DIAG)
-                step_reg<DIAG, false, true>(c, l, r, av, top, k, s32, n32, m1, m2, mneg, mhalf);
+            if (kRegm && CONSTR && DIAG)
+                step_reg<DIAG, true, true>(c, l, r, av, top, k, s32, n32, m1, m2, mneg, mhalf);
+            else if (kRegm && CONSTR)
+                step_regm_constr(c, l, r, av, top, k.stride, k.table, k.thr, s32, m1, m2, mneg,
+                                 mhalf);
+            else if (kRegm && DIAG)
+                step_reg<DIAG, false, true, kPushLast, kSplit>(c, l, r, av, top, k, s32, n32, m1,
+                                                               m2, mneg, mhalf);
             else if (kRegm)
-                step_regm(c, l, r, av, top, k.stride, s32, m1, m2, mneg, mhalf);
+                step_regm<kPushLast, kSplit>(c, l, r, av, top, k.stride, s32, m1, m2, mneg,
+                                             mhalf);
             else if (kReg)
                 step_reg<DIAG, CONSTR>(c, l, r, av, top, k, s32, n32);
             else if (kWt)
@@ -922,9 +1063,11 @@ __global__ void __maxnreg__(64) serve_kernel(const ServeArgs a) {
     const unsigned lane = threadIdx.x & 31u;
     const unsigned lt_mask = (1u << lane) - 1u;
 
-    uint32_t c = kSentinelC, l = ~0u, r = ~0u, av = kSentinelAvC;
-    uint32_t top = k.base;
-    sts4(k.base, make_uint4(kSentinelC, ~0u, ~0u, kSentinelAvC));
+    // two sentinel frames (slots 0 and 1): an idle lane runs whole rounds on them
+    uint32_t c = kSentinelC, l = kSentinelLrC, r = kSentinelLrC, av = kSentinelAvC;
+    uint32_t top = k.base + k.stride;
+    sts4(k.base, make_uint4(kSentinelC, kSentinelLrC, kSentinelLrC, kSentinelAvC));
+    sts4(k.base + k.stride, make_uint4(kSentinelC, kSentinelLrC, kSentinelLrC, kSentinelAvC));
     int cur_slot = -1;
     uint32_t cur_w = 1;  // symmetry weight of the record being searched
     uint64_t sol = 0;
@@ -952,15 +1095,16 @@ __global__ void __maxnreg__(64) serve_kernel(const ServeArgs a) {
     };
 
     for (;;) {
-        const bool idle = top == k.base;
+        const bool idle = top <= k.base + k.stride;
         if (idle) {
             if (cur_slot >= 0) {
                 finish_slot(cur_slot, sol * cur_w);
                 cur_slot = -1;
             }
             c = kSentinelC;
-            l = r = ~0u;
+            l = r = kSentinelLrC;
             av = kSentinelAvC;
+            top = k.base + k.stride;
         }
         bool need = idle;
         unsigned need_mask = __ballot_sync(~0u, need);
@@ -1024,10 +1168,11 @@ __global__ void __maxnreg__(64) serve_kernel(const ServeArgs a) {
                 const uint32_t n = (P.w >> 2) & 31u, d = (P.w >> 7) & 31u, w = P.w & 3u;
                 const int slot = (int)(P.w >> 12);
                 const uint32_t last = (n >= 1u) ? (0xFFFFFFFFu >> (32u - n)) : 0u;
+                // (stack: two sentinels + the ancestors of rows d..N-3)
                 const bool ok = slot < a.nslots && n >= 1u && n <= (uint32_t)kMaxConstrainedN &&
                                 (w == 1u || w == 2u) &&
                                 d <= n && (P.x & ~last) == 0u && (uint32_t)__popc(P.x) == d &&
-                                (d + 1u >= n || (int)n - 1 - (int)d <= a.slots);
+                                (d + 1u >= n || (int)n - (int)d <= a.slots);
                 if (!ok) {
                     record_error(k.status, NQ_EINVAL);
                     if (slot < a.nslots) finish_slot(slot, 0);
@@ -1057,7 +1202,7 @@ __global__ void __maxnreg__(64) serve_kernel(const ServeArgs a) {
                         k.table = tab;
                         k.thr = (n - 1u) << kRowShift;
                         c = c0; l = l0; r = r0; av = a0;
-                        top = k.base + k.stride;
+                        top = k.base + 2u * k.stride;  // above the two sentinels
                         need = false;
                     }
                 }
@@ -1066,7 +1211,7 @@ __global__ void __maxnreg__(64) serve_kernel(const ServeArgs a) {
             need_mask = __ballot_sync(~0u, need);
             if (got < asked) break;  // the ring is drained for now
         }
-        if (__all_sync(~0u, top == k.base && cur_slot < 0)) {
+        if (__all_sync(~0u, top <= k.base + k.stride && cur_slot < 0)) {
             // (plain stores to the mapped block: no atomics on host memory)
             if (stopping) {
                 if (lane == 0) a.ctl->exit_reason = 1;
@@ -1097,9 +1242,13 @@ __global__ void __maxnreg__(64) serve_kernel(const ServeArgs a) {
             continue;
         }
         idle_polls = 0;
-        uint32_t s32 = 0, n32 = 0;
+        uint32_t s32 = 0;
+        const uint32_t m1 = a.mul[0], m2 = a.mul[1], mneg = a.mul[2], mhalf = a.mul[3];
+        // two 27-step sentinels: 31 steps between bookkeeping points
 #pragma unroll
-        for (int j = 0; j < kChunk; ++j) step_reg<false, true>(c, l, r, av, top, k, s32, n32);
+        for (int j = 0; j < 31; ++j)
+            step_regm_constr(c, l, r, av, top, k.stride, k.table, k.thr, s32, m1, m2, mneg,
+                             mhalf);
         sol += s32;
     }
 }
@@ -1130,51 +1279,59 @@ void *kernel_ptr() {
         return reinterpret_cast<void *>(&search_kernel<LAYOUT, DIAG, CONSTR>);
 }
 
+template <int LAYOUT>
+void *stream_ptr(bool diag) {
+    return diag ? reinterpret_cast<void *>(&search_kernel_stream<LAYOUT, true>)
+                : reinterpret_cast<void *>(&search_kernel_stream<LAYOUT, false>);
+}
+template <int LAYOUT>
+void *plain_ptr(bool diag) {
+    return diag ? kernel_ptr<LAYOUT, true, false>() : kernel_ptr<LAYOUT, false, false>();
+}
+
 void *pick_kernel(int layout, bool diag, bool constrained, bool donate = false,
                   bool stream = false) {
-    if (stream && layout == NQ_LAYOUT_REGM)
-        return diag ? reinterpret_cast<void *>(&search_kernel_stream<NQ_LAYOUT_REGM, true>)
-                    : reinterpret_cast<void *>(&search_kernel_stream<NQ_LAYOUT_REGM, false>);
-    if (stream && layout == NQ_LAYOUT_REG)
-        return diag ? reinterpret_cast<void *>(&search_kernel_stream<NQ_LAYOUT_REG, true>)
-                    : reinterpret_cast<void *>(&search_kernel_stream<NQ_LAYOUT_REG, false>);
+    if (stream) {
+        switch (layout) {
+            case NQ_LAYOUT_REGM: return stream_ptr<NQ_LAYOUT_REGM>(diag);
+            case NQ_LAYOUT_REGP: return stream_ptr<NQ_LAYOUT_REGP>(diag);
+            case NQ_LAYOUT_REGZ: return stream_ptr<NQ_LAYOUT_REGZ>(diag);
+            case NQ_LAYOUT_REGPZ: return stream_ptr<NQ_LAYOUT_REGPZ>(diag);
+            default: return stream_ptr<NQ_LAYOUT_REG>(diag);
+        }
+    }
     if (constrained)
-        return diag ? kernel_ptr<NQ_LAYOUT_REG, true, true>()
-                    : kernel_ptr<NQ_LAYOUT_REG, false, true>();
+        return diag ? kernel_ptr<NQ_LAYOUT_REGM, true, true>()
+                    : kernel_ptr<NQ_LAYOUT_REGM, false, true>();
     if (donate && layout == NQ_LAYOUT_REGM)
         return diag ? kernel_ptr<NQ_LAYOUT_REGM, true, false, true>()
                     : kernel_ptr<NQ_LAYOUT_REGM, false, false, true>();
     if (donate && layout == NQ_LAYOUT_REG)
         return diag ? kernel_ptr<NQ_LAYOUT_REG, true, false, true>()
                     : kernel_ptr<NQ_LAYOUT_REG, false, false, true>();
-    if (layout == NQ_LAYOUT_PAPER)
-        return diag ? kernel_ptr<NQ_LAYOUT_PAPER, true, false>()
-                    : kernel_ptr<NQ_LAYOUT_PAPER, false, false>();
-    if (layout == NQ_LAYOUT_WT)
-        return diag ? kernel_ptr<NQ_LAYOUT_WT, true, false>()
-                    : kernel_ptr<NQ_LAYOUT_WT, false, false>();
-    if (layout == NQ_LAYOUT_WT32)
-        return diag ? kernel_ptr<NQ_LAYOUT_WT32, true, false>()
-                    : kernel_ptr<NQ_LAYOUT_WT32, false, false>();
-    if (layout == NQ_LAYOUT_WT32A)
-        return diag ? kernel_ptr<NQ_LAYOUT_WT32A, true, false>()
-                    : kernel_ptr<NQ_LAYOUT_WT32A, false, false>();
-    if (layout == NQ_LAYOUT_WTM)
-        return diag ? kernel_ptr<NQ_LAYOUT_WTM, true, false>()
-                    : kernel_ptr<NQ_LAYOUT_WTM, false, false>();
-    if (layout == NQ_LAYOUT_REGM)
-        return diag ? kernel_ptr<NQ_LAYOUT_REGM, true, false>()
-                    : kernel_ptr<NQ_LAYOUT_REGM, false, false>();
-    return diag ? kernel_ptr<NQ_LAYOUT_REG, true, false>()
-                : kernel_ptr<NQ_LAYOUT_REG, false, false>();
+    switch (layout) {
+        case NQ_LAYOUT_PAPER: return plain_ptr<NQ_LAYOUT_PAPER>(diag);
+        case NQ_LAYOUT_WT: return plain_ptr<NQ_LAYOUT_WT>(diag);
+        case NQ_LAYOUT_WT32: return plain_ptr<NQ_LAYOUT_WT32>(diag);
+        case NQ_LAYOUT_WT32A: return plain_ptr<NQ_LAYOUT_WT32A>(diag);
+        case NQ_LAYOUT_WTM: return plain_ptr<NQ_LAYOUT_WTM>(diag);
+        case NQ_LAYOUT_REGM: return plain_ptr<NQ_LAYOUT_REGM>(diag);
+        case NQ_LAYOUT_REGP: return plain_ptr<NQ_LAYOUT_REGP>(diag);
+        case NQ_LAYOUT_REGZ: return plain_ptr<NQ_LAYOUT_REGZ>(diag);
+        case NQ_LAYOUT_REGPZ: return plain_ptr<NQ_LAYOUT_REGPZ>(diag);
+        default: return plain_ptr<NQ_LAYOUT_REG>(diag);
+    }
 }
 
 }  // namespace
 
 int slots_needed(int layout, int max_n, int min_d) {
-    const bool reg = layout == NQ_LAYOUT_REG || layout == NQ_LAYOUT_REGM;
+    const bool reg = layout_register_top(layout);
+    // REG: a sentinel + ancestors of rows d..N-3; with the last row pushed,
+    // rows d..N-2; WT / PAPER: a sentinel + frames of rows d..N-2
     int s = reg ? max_n - 1 - min_d : max_n - min_d;
-    if (layout == NQ_LAYOUT_REGM) s = (s < 1 ? 1 : s) + 1;  // the second sentinel frame
+    if (layout == NQ_LAYOUT_REGP || layout == NQ_LAYOUT_REGPZ) s += 1;
+    if (layout_regm_family(layout)) s = (s < 1 ? 1 : s) + 1;  // the second sentinel frame
     return s < 1 ? 1 : s;
 }
 
@@ -1190,22 +1347,23 @@ int make_plan(int max_n, int min_d, bool diag, bool constrained, const nq_config
         return NQ_ECUDA;
     Plan p{};
     p.layout = (cfg && cfg->layout) ? cfg->layout : NQ_LAYOUT_REGM;
-    if (p.layout < NQ_LAYOUT_PAPER || p.layout > NQ_LAYOUT_REGM) return NQ_EINVAL;
-    if (constrained) p.layout = NQ_LAYOUT_REG;
+    if (p.layout < NQ_LAYOUT_PAPER || p.layout > NQ_LAYOUT_LAST) return NQ_EINVAL;
+    if (constrained) p.layout = NQ_LAYOUT_REGM;  // the constrained multiply-add step
     p.block = (cfg && cfg->block) ? cfg->block : 256;
     if (p.block < 32 || p.block > 1024 || p.block % 32) return NQ_EINVAL;
+    // split-word kernels are compiled for one block size
+    if (layout_split_words(p.layout) && p.block != (int)kZBlock) return NQ_EINVAL;
     p.slots = slots_needed(p.layout, max_n, min_d);
     const size_t per_thread = (size_t)p.slots * 16u;
     const size_t extra = constrained ? 32u * 4u : 0u;
     if ((size_t)p.block * per_thread + extra > (size_t)max_smem) {
         int fit = (int)(((size_t)max_smem - extra) / per_thread) / 32 * 32;
-        if (fit < 32) return NQ_ESTACK;
+        if (fit < 32 || layout_split_words(p.layout)) return NQ_ESTACK;
         p.block = fit;
     }
     p.smem = (size_t)p.block * per_thread + extra;
     p.donate = donate && (p.layout == NQ_LAYOUT_REG || p.layout == NQ_LAYOUT_REGM) && !constrained;
-    p.stream = stream && !p.donate && !constrained &&
-               (p.layout == NQ_LAYOUT_REG || p.layout == NQ_LAYOUT_REGM);
+    p.stream = stream && !p.donate && !constrained && layout_register_top(p.layout);
     if (stream && !p.stream) return NQ_EINVAL;
     void *k = pick_kernel(p.layout, diag, constrained, p.donate, p.stream);
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem) !=
@@ -1244,7 +1402,7 @@ int serve_plan(int max_n, int min_d, int nslots, int block, int *grid, size_t *s
         cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) !=
             cudaSuccess)
         return NQ_ECUDA;
-    const int sl = slots_needed(NQ_LAYOUT_REG, max_n, min_d);
+    const int sl = slots_needed(NQ_LAYOUT_REGM, max_n, min_d);  // two sentinels
     const size_t bytes = (size_t)sl * 16u * block + (size_t)nslots * 132u;
     if (bytes > (size_t)max_smem) return NQ_ESTACK;
     void *k = reinterpret_cast<void *>(&serve_kernel);

@@ -20,7 +20,8 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 Q = {int(k): v for k, v in json.load(open(os.path.join(GOLDEN, "oeis_a000170.json")))["Q"].items()}
-LAYOUTS = ["paper", "reg", "wt", "wt32", "wt32a", "wtm", "regm"]
+LAYOUTS = ["paper", "reg", "wt", "wt32", "wt32a", "wtm", "regm", "regp", "regz", "regpz"]
+SPLIT_WORDS = {"regz", "regpz"}  # compiled for 256-thread blocks
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -129,7 +130,10 @@ def test_launch_shapes(orc, layout):
     n, d = 13, 4
     pre = nq.enumerate_prefixes(n, d)
     want, _ = oracle_counts(orc, n, d)
-    for block, bps, order in [(32, 1, 0), (64, 3, 1), (128, 0, 2), (512, 1, 1), (1024, 0, 0)]:
+    shapes = [(32, 1, 0), (64, 3, 1), (128, 0, 2), (512, 1, 1), (1024, 0, 0)]
+    if layout in SPLIT_WORDS:
+        shapes = [(256, 1, 0), (256, 3, 1), (256, 0, 2)]
+    for block, bps, order in shapes:
         got, _, tot = run(pre, d, n, layout, block=block, blocks_per_sm=bps, order=order)
         assert np.array_equal(got, want), (block, bps, order)
         assert int(tot[n]) == Q[n]
@@ -215,7 +219,7 @@ def records_of(n, placements):
     return pre
 
 
-@pytest.mark.parametrize("layout", ["regm", "reg", "paper"])
+@pytest.mark.parametrize("layout", ["regm", "reg", "paper", "regp", "regz", "regpz"])
 @pytest.mark.parametrize("n", [29, 30, 31])
 def test_widest_boards(orc, layout, n):
     """The widest boards the 32-bit masks allow (N = 31 leaves one pre-set high
@@ -400,3 +404,21 @@ def test_host_split_rejects_bad_input():
         nq.count_split(pre, 2)
     r = nq.count_split(pre[:0], 2)
     assert len(r["counts"]) == 0 and int(r["totals"].sum()) == 0
+
+
+def test_split_word_layouts_need_256_thread_blocks():
+    pre = nq.enumerate_prefixes(10, 3)
+    dp = nq.to_device(pre)
+    cnt = torch.zeros(len(pre), dtype=torch.int64, device="cuda")
+    for layout in sorted(SPLIT_WORDS):
+        with pytest.raises(nq.NQError) as e:
+            nq.count_ex(dp, 3, 10, cnt, None, None, nq.make_config(layout, 128))
+        assert e.value.code == nq.NQ_EINVAL
+
+
+@pytest.mark.parametrize("layout", ["regp", "regz", "regpz"])
+def test_streamed_total_new_layouts(layout):
+    """nq_total_ex streams N=18's d=7 set (7.4 M records) into the running search
+    in every register-top layout."""
+    r = nq.total_ex(18, nq.make_config(layout, d=7))
+    assert r["total"] == Q[18] and r["layout"] == nq.LAYOUTS[layout]

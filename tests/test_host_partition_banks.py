@@ -91,13 +91,18 @@ ACCESSES = {
     "paper": [(0, 16)], "reg": [(0, 16)], "regm": [(0, 16)],
     "wt": [(0, 16), (3, 4)], "wtm": [(0, 16), (3, 4)],
     "wt32": [(0, 4), (1, 4), (2, 4), (3, 4)], "wt32a": [(0, 4), (1, 4), (2, 4), (3, 4)],
+    "regp": [(0, 16)],
+    "regz": [(0, 4), (1, 4), (2, 4), (3, 4)], "regpz": [(0, 4), (1, 4), (2, 4), (3, 4)],
 }
+SPLIT_WORDS = {"regz", "regpz"}  # built for 256-thread blocks only
 KNOWN_4WAY = {("wt", 3), ("wtm", 3)}  # the lone avail-word stores of WT and WTM
 
 
 @pytest.mark.parametrize("layout", sorted(ACCESSES))
 @pytest.mark.parametrize("block", [64, 128, 160, 192, 256, 512])
 def test_stack_layouts_bank_conflicts(layout, block):
+    if layout in SPLIT_WORDS and block != 256:
+        pytest.skip("split-word frames are compiled for 256-thread blocks")
     rng = np.random.default_rng(block)
     slots = 12
     for trial in range(40):
@@ -126,3 +131,21 @@ def test_stack_offset_rejects_bad_arguments():
                  ("regm", 256, 8, 0, 8, 0), ("regm", 256, 8, 0, 0, 4)]:
         with pytest.raises(nq.NQError):
             nq.stack_offset(*args)
+
+
+@pytest.mark.parametrize("layout", sorted(SPLIT_WORDS))
+def test_split_words_one_bank_per_lane(layout):
+    """Split-word frames: every word of thread t sits in bank t mod 32, at any
+    slot and field, so a warp's 32-bit accesses -- by any subset of lanes, at any
+    mix of depths -- touch distinct banks (one wavefront, nothing to conflict)."""
+    for t in range(256):
+        for slot in (0, 1, 5, 11):
+            for field in range(4):
+                off = nq.stack_offset(layout, 256, 12, t, slot, field)
+                assert off % 4 == 0 and (off // 4) % 32 == t % 32
+    # distinct words for distinct (thread, slot, field)
+    offs = {nq.stack_offset(layout, 256, 12, t, k, f)
+            for t in range(256) for k in range(12) for f in range(4)}
+    assert len(offs) == 256 * 12 * 4 and max(offs) < 256 * 12 * 16
+    with pytest.raises(nq.NQError):
+        nq.stack_offset(layout, 128, 12, 0, 0, 0)
