@@ -338,23 +338,53 @@ def run_batched(args, device, local):
     print(json.dumps(line), flush=True)
 
 
+def _oracle_constrained(job):
+    import oracle
+    n, queens = job
+    return oracle.count_constrained(n, queens)[0]
+
+
+def check_served_answers(reqs: list[dict], answers: dict, seed: int = 77,
+                         sample: int = 384, heavy: int = 32) -> dict:
+    """Exactness of the served answers against references that share nothing
+    with the CUDA path: every request without queens against OEIS A000170,
+    and a seeded sample of the requests with queens against the CPU oracle's
+    constrained backtracker (run in a spawned process pool, after the timed
+    runs): `sample` of those with N <= 16 and `heavy` with N in 17..18 (the
+    oracle needs minutes per request beyond that)."""
+    import multiprocessing as mp
+    import synth_inputs
+    q = json.load(open(os.path.join(ROOT, "tests", "golden", "oeis_a000170.json")))["Q"]
+    bad = [i for i, r in enumerate(reqs) if not r["queens"] and answers[i] != q[str(r["n"])]]
+    k0 = sum(1 for r in reqs if not r["queens"])
+    light = [i for i, r in enumerate(reqs) if r["queens"] and r["n"] <= 16]
+    mid = [i for i, r in enumerate(reqs) if r["queens"] and 17 <= r["n"] <= 18]
+    pick = [light[j] for j in synth_inputs.sample_indices(seed, len(light), sample)]
+    pick += [mid[j] for j in synth_inputs.sample_indices(seed + 1, len(mid), heavy)]
+    t0 = time.perf_counter()
+    with mp.get_context("spawn").Pool(os.cpu_count() or 1) as pool:
+        want = pool.map(_oracle_constrained, [(reqs[i]["n"], reqs[i]["queens"]) for i in pick],
+                        chunksize=1)
+    bad += [i for i, w in zip(pick, want) if answers[i] != w]
+    return {"unconstrained_vs_oeis": k0, "constrained_vs_oracle": len(pick),
+            "oracle_s": time.perf_counter() - t0, "mismatches": len(bad), "exact": not bad}
+
+
 def run_served(args, device, local):
     """Seeded Poisson streams at fractions of the measured capacity."""
     import synth_inputs
-    from paper_2511_12009_gb300 import nq
     from paper_2511_12009_gb300.serve import Server, run_stream
-    q = json.load(open(os.path.join(ROOT, "tests", "golden", "oeis_a000170.json")))["Q"]
     reqs = synth_inputs.request_stream(2024, args.requests, 10, 20, 0, 4, rate_per_s=1.0)
     # capacity: every request due at once
     sat = [dict(r, t=0.0) for r in reqs]
     clocks = ClockSampler(local)
     clocks.start()
     with Server(max_n=20, request_slots=64, idle_ms=200) as srv:
-        res = run_stream(srv, sat, timeout_s=3600)
+        res = run_stream(srv, sat, timeout_s=7200)
     capacity = len(reqs) / res["wall_s"]
     print(f"served: saturation run {res['wall_s']:.1f} s, {capacity:.2f} requests/s",
           file=sys.stderr, flush=True)
-    runs = [{"load": "saturation", "wall_s": res["wall_s"],
+    runs = [{"load": "saturation", "wall_s": res["wall_s"], "requests_per_s": capacity,
              "p50_ms": 1e3 * float(np.percentile(list(res["latency_s"].values()), 50)),
              "p99_ms": 1e3 * float(np.percentile(list(res["latency_s"].values()), 99))}]
     answers = res["answers"]
@@ -364,7 +394,7 @@ def run_served(args, device, local):
         rate = load * capacity
         stream = synth_inputs.request_stream(2024, args.requests, 10, 20, 0, 4, rate_per_s=rate)
         with Server(max_n=20, request_slots=64, idle_ms=200) as srv:
-            r = run_stream(srv, stream, timeout_s=3600)
+            r = run_stream(srv, stream, timeout_s=7200)
         lat = list(r["latency_s"].values())
         print(f"served: load {load} run {r['wall_s']:.1f} s", file=sys.stderr, flush=True)
         if r["answers"] != answers:
@@ -373,11 +403,7 @@ def run_served(args, device, local):
                      "p50_ms": 1e3 * float(np.percentile(lat, 50)),
                      "p99_ms": 1e3 * float(np.percentile(lat, 99))})
     clk = clocks.stop()
-    # exactness: unconstrained boards against the published table; a sample against
-    # the standalone constrained count (the same request alone)
-    bad = [i for i, r in enumerate(reqs) if not r["queens"] and answers[i] != q[str(r["n"])]]
-    sample = list(range(0, len(reqs), max(1, len(reqs) // 50)))
-    bad += [i for i in sample if answers[i] != nq.count_constrained(reqs[i]["n"], reqs[i]["queens"])]
+    check = check_served_answers(reqs, answers)
     line = {"metric": METRIC, "value": capacity, "unit": "requests/s", "n_gpus": 1,
             "steps": len(runs), "warmup": 0, "ms_per_step": 1e3 * runs[0]["wall_s"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
@@ -385,8 +411,7 @@ def run_served(args, device, local):
             "config": {"workload": f"served: {len(reqs)} seeded requests, N uniform in [10, 20], "
                                    "0-4 non-attacking queens, Poisson arrivals",
                        "request_slots": 64, "stack_slots": 12},
-            "runs": runs, "answers_checked": len(sample), "answers_exact": not bad,
-            "clocks": clk}
+            "runs": runs, "answers": check, "answers_exact": check["exact"], "clocks": clk}
     print(json.dumps(line), flush=True)
 
 

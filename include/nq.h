@@ -105,10 +105,11 @@ typedef struct nq_queen {
 #define NQ_LAYOUT_WTM 6   /* WT with the step's disjoint-bit arithmetic written as
                              integer multiply-adds, balancing the FMA and ALU pipes */
 #define NQ_LAYOUT_REGM 7  /* REG with the same multiply-add arithmetic, the control tail as
-                             one predicated block (the default) */
+                             one predicated block */
 #define NQ_LAYOUT_REGP 8  /* REGM without the last-row rule: the row N-1 child is pushed and
                              a solution is the step that fills every column (one compare
-                             instead of a population count; one more frame per thread) */
+                             instead of a population count; one more frame per thread).
+                             The default. */
 #define NQ_LAYOUT_REGZ 9  /* REGM with each frame saved and restored as four 32-bit words
                              in four arrays, every word in its lane's own bank: zero bank
                              conflicts for any set of active lanes (256-thread blocks) */

@@ -334,7 +334,7 @@ extern "C" int nq_total_ex(int N, const nq_config *cfg, uint64_t *total_out, uin
     }
     // streamed input needs a register-stack layout (the default); any other
     // layout searches once every piece is in
-    const int lay = cfg->layout ? cfg->layout : NQ_LAYOUT_REGM;
+    const int lay = cfg->layout ? cfg->layout : NQ_LAYOUT_DEFAULT_SEARCH;
     const bool stream_in = npieces > 1 && layout_register_top(lay);
     cudaEventRecord(ev[0], ctx.s);
     rc = cuda_rc(cudaMemsetAsync(d_tot, 0, 32 * sizeof(uint64_t), ctx.s));

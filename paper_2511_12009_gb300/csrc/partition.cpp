@@ -33,7 +33,7 @@ extern "C" int nq_partition(uint64_t n, const float *ratios, int k, uint64_t *fi
 
 extern "C" int nq_stack_offset(int layout, int block, int slots, int thread, int slot, int field,
                                uint32_t *offset_out) {
-    if (layout == NQ_LAYOUT_DEFAULT) layout = NQ_LAYOUT_REGM;
+    if (layout == NQ_LAYOUT_DEFAULT) layout = nqi::NQ_LAYOUT_DEFAULT_SEARCH;
     if (layout < NQ_LAYOUT_PAPER || layout > NQ_LAYOUT_LAST || block < 32 || block > 1024 ||
         block % 32 || slots < 1 || slots > 64 || thread < 0 || thread >= block || slot < 0 ||
         slot >= slots || field < 0 || field > 3 || !offset_out)

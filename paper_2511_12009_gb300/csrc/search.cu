@@ -1175,6 +1175,7 @@ __global__ void __maxnreg__(64) serve_kernel(const ServeArgs a) {
                                 (d + 1u >= n || (int)n - (int)d <= a.slots);
                 if (!ok) {
                     record_error(k.status, NQ_EINVAL);
+                    a.ctl->error = NQ_EINVAL;  // mapped: the next poll reports it
                     if (slot < a.nslots) finish_slot(slot, 0);
                 } else {
                     // the slot's allowed masks, cached in this block's shared memory
@@ -1346,7 +1347,7 @@ int make_plan(int max_n, int min_d, bool diag, bool constrained, const nq_config
             cudaSuccess)
         return NQ_ECUDA;
     Plan p{};
-    p.layout = (cfg && cfg->layout) ? cfg->layout : NQ_LAYOUT_REGM;
+    p.layout = (cfg && cfg->layout) ? cfg->layout : NQ_LAYOUT_DEFAULT_SEARCH;
     if (p.layout < NQ_LAYOUT_PAPER || p.layout > NQ_LAYOUT_LAST) return NQ_EINVAL;
     if (constrained) p.layout = NQ_LAYOUT_REGM;  // the constrained multiply-add step
     p.block = (cfg && cfg->block) ? cfg->block : 256;
@@ -1361,11 +1362,33 @@ int make_plan(int max_n, int min_d, bool diag, bool constrained, const nq_config
         if (fit < 32 || layout_split_words(p.layout)) return NQ_ESTACK;
         p.block = fit;
     }
-    p.smem = (size_t)p.block * per_thread + extra;
     p.donate = donate && (p.layout == NQ_LAYOUT_REG || p.layout == NQ_LAYOUT_REGM) && !constrained;
     p.stream = stream && !p.donate && !constrained && layout_register_top(p.layout);
     if (stream && !p.stream) return NQ_EINVAL;
     void *k = pick_kernel(p.layout, diag, constrained, p.donate, p.stream);
+    if (!(cfg && cfg->block) && !layout_split_words(p.layout)) {
+        // No block size asked for: the one that keeps the most threads resident
+        // per SM under this stack footprint (ties: the larger block). A frame
+        // more per thread (deeper boards, REGP) can cost a whole block per SM
+        // at 256 threads and none at 192 or 224.
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, max_smem) !=
+            cudaSuccess)
+            return NQ_ECUDA;
+        int best = 0, best_threads = 0;
+        for (int b : {256, 224, 192, 160, 128}) {
+            const size_t sm = (size_t)b * per_thread + extra;
+            if (sm > (size_t)max_smem) continue;
+            int nb = 0;
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, b, sm) != cudaSuccess)
+                return NQ_ECUDA;
+            if (nb * b > best_threads) {
+                best = b;
+                best_threads = nb * b;
+            }
+        }
+        if (best) p.block = best;
+    }
+    p.smem = (size_t)p.block * per_thread + extra;
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem) !=
         cudaSuccess)
         return NQ_ECUDA;

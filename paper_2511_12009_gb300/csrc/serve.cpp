@@ -213,6 +213,7 @@ extern "C" int nq_server_create(const nq_server_config *cfg, nq_server **out) {
     s->h_ctl->head = 0;
     s->h_ctl->stop = 0;
     s->h_ctl->exit_reason = 0;
+    s->h_ctl->error = 0;
     for (int i = 0; i < c.request_slots; ++i) {
         s->h_done[i].seq = 0;
         s->h_done[i].total = 0;
@@ -251,7 +252,9 @@ extern "C" int nq_server_submit(nq_server *s, int N, const nq_queen *q, int k, u
     // resident lane -- a few heavy subtrees would leave most lanes idle while
     // they finish -- as long as the next depth's records take at most a
     // quarter of the ring.
-    int d = std::min(N, std::max(N - 1 - s->stack_slots, std::min(N - 2 < 0 ? 0 : N - 2, 5)));
+    // (the kernel's stack holds two sentinel frames and N - 2 - d ancestors:
+    // N - d <= s->stack_slots)
+    int d = std::min(N, std::max(N - s->stack_slots, std::min(N - 2 < 0 ? 0 : N - 2, 5)));
     {
         auto count_at = [&](int dd) -> uint64_t {
             uint64_t np = 0;
@@ -345,12 +348,17 @@ extern "C" int nq_server_poll(nq_server *s, uint64_t *tickets, uint64_t *counts,
     bool pending = false;
     for (const auto &r : s->req) pending = pending || r.active;
     int rc = NQ_OK;
+    if (s->h_ctl->error) {  // raised by the kernel while it runs
+        rc = s->h_ctl->error;
+        s->h_ctl->error = 0;
+    }
     if (s->launched) {
         const cudaError_t q = cudaEventQuery(s->kdone);
         if (q != cudaSuccess && q != cudaErrorNotReady) return NQ_ECUDA;
         if (q == cudaSuccess) {
             // the kernel has left: its error word is final (read before any relaunch)
-            rc = nqi::take_status(s->status(), s->cstream);
+            const int st = nqi::take_status(s->status(), s->cstream);
+            if (!rc) rc = st;
             // it left (idle) while work was being published: start it again
             if (pending) {
                 const int lrc = ensure_running(s);

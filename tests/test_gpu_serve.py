@@ -37,6 +37,32 @@ def test_stream_matches_oracle_and_standalone(orc):
             assert nq.count_constrained(r["n"], r["queens"]) == want
 
 
+@pytest.mark.parametrize("max_n,slots", [(16, 6), (17, 12), (20, 12)])
+def test_largest_boards_at_the_stack_limit(orc, max_n, slots):
+    """Requests at the server's largest board size, where the depth the stack
+    footprint forces (N - 1 - d frames) decides whether a record fits: answers
+    against the standalone count and, for small boards, the oracle; boards
+    without queens against OEIS."""
+    from paper_2511_12009_gb300.serve import Server, run_stream
+    g = synth_inputs.SplitMix64(4000 + max_n)
+    reqs = []
+    for i in range(12):
+        k = [0, 1, 2][i % 3]
+        reqs.append({"id": i, "t": 0.0, "n": max_n,
+                     "queens": synth_inputs.constraint_set(g, max_n, k)})
+    with Server(max_n=max_n, stack_slots=slots, request_slots=16, idle_ms=100) as srv:
+        res = run_stream(srv, reqs, timeout_s=600)
+        assert srv.poll() == []      # no error surfaced after the last answer
+    for i, r in enumerate(reqs):
+        if not r["queens"]:
+            assert res["answers"][i] == Q[max_n]
+        else:
+            want = nq.count_constrained(max_n, r["queens"])
+            assert res["answers"][i] == want, (r["queens"],)
+            if max_n <= 16:
+                assert want == orc.count_constrained(max_n, r["queens"])[0]
+
+
 def test_light_requests_overtake_a_heavy_one():
     from paper_2511_12009_gb300.serve import Server
     with Server(max_n=20, request_slots=64, idle_ms=200) as srv:
