@@ -76,7 +76,7 @@ def parse():
     ap.add_argument("--d", type=int, default=0, help="prefix depth (0 = library default)")
     ap.add_argument("--layout", default="default",
                     choices=["default", "paper", "reg", "wt", "wt32", "wt32a", "wtm", "regm",
-                             "regp", "regz", "regpz"])
+                             "regp", "regz", "regpz", "avail"])
     ap.add_argument("--block", type=int, default=0)
     ap.add_argument("--bps", type=int, default=0, help="blocks per SM (0 = max)")
     ap.add_argument("--order", type=int, default=0, help="0 default, 1 index order, 2 reverse")
@@ -292,19 +292,15 @@ def run_batched(args, device, local):
     from paper_2511_12009_gb300 import nq
     from paper_2511_12009_gb300.batch import Batch
     ns = [16, 17, 18, 19, 20, 21]
-    ds = [nq.default_depth(n) for n in ns]
+    # the autotuner's staged search over depths, layout, block / order and
+    # claim chunk for the one launch (graph replays), then the tuned batch timed
+    from paper_2511_12009_gb300 import tune
+    tuned = tune.tune_batch(ns, reps=1)
+    ds = tuned["ds"]
+    best = nq.make_config(**tuned["config"])
     nodes = 0
-    for n, d in zip(ns, ds):  # node counts of the same work (diagnostic build, untimed)
+    for n, d in zip(ns, ds):  # node counts of the tuned depths (diagnostic build, untimed)
         nodes += nq.total_ex(n, nq.make_config(d=d), nodes=True)["nodes"]
-    # reduced tuning of the one launch: block size and order (depths as above)
-    best, best_ms = None, None
-    for block in (128, 256):
-        for order in (0,):
-            cfg = nq.make_config("regm", block, 0, order)
-            with Batch(ns, ds, cfg) as b:
-                _, ms = b.run()
-            if best_ms is None or ms < best_ms:
-                best, best_ms = cfg, ms
     stream = torch.cuda.current_stream(device)
     clocks = ClockSampler(local)
     with Batch(ns, ds, best) as b:
@@ -331,6 +327,8 @@ def run_batched(args, device, local):
                                    "launch replayed from a CUDA graph",
                        "ns": ns, "ds": ds, "records": info["records"], "grid": info["grid"],
                        "block": info["block"], "nodes_per_step": nodes,
+                       "tuned": {"config": tuned["config"], "candidates": len(tuned["tried"]),
+                                 "best_candidate_ms": tuned["ms"]},
                        "l2": "inputs resident; no flush (compute-bound, one pass)"},
             "separate_launches_ms": float(np.mean(sep_ms)),
             "graph_vs_separate": float(np.mean(sep_ms)) / g, "totals_exact": exact,

@@ -114,11 +114,15 @@ typedef struct nq_queen {
                              in four arrays, every word in its lane's own bank: zero bank
                              conflicts for any set of active lanes (256-thread blocks) */
 #define NQ_LAYOUT_REGPZ 10 /* REGP with REGZ's split-word frames */
-#define NQ_LAYOUT_LAST NQ_LAYOUT_REGPZ
+#define NQ_LAYOUT_AVAIL 11 /* the avail-only stack: one 32-bit word per level (the level's
+                              candidates), the parent state restored by undoing the
+                              placement; 4 bytes of shared memory per level, every access
+                              a word in the lane's own bank; N <= 30 */
+#define NQ_LAYOUT_LAST NQ_LAYOUT_AVAIL
 
 /* Launch configuration. Zero in any field selects the default: for layout,
  * block, claim and d the environment variables NQ_LAYOUT (a layout number or
- * name: paper, reg, wt, wt32, wt32a, wtm, regm, regp, regz, regpz), NQ_BLOCK,
+ * name: paper, reg, wt, wt32, wt32a, wtm, regm, regp, regz, regpz, avail), NQ_BLOCK,
  * NQ_CLAIM and NQ_D
  * when set to a valid value, else the library's own default. (Batches take
  * their configuration as given.) */

@@ -43,7 +43,7 @@ int env_layout() {
     const char *v = std::getenv("NQ_LAYOUT");
     if (!v || !*v) return 0;
     static const char *names[] = {"default", "paper", "reg",  "wt",   "wt32",  "wt32a",
-                                  "wtm",     "regm",  "regp", "regz", "regpz"};
+                                  "wtm",     "regm",  "regp", "regz", "regpz", "avail"};
     static_assert(sizeof(names) / sizeof(names[0]) == NQ_LAYOUT_LAST + 1, "one name per layout");
     for (int i = 0; i <= NQ_LAYOUT_LAST; ++i)
         if (std::strcmp(v, names[i]) == 0) return i;

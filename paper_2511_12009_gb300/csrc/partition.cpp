@@ -44,6 +44,11 @@ extern "C" int nq_stack_offset(int layout, int block, int slots, int thread, int
                                              (uint32_t)slot, (uint32_t)field);
         return NQ_OK;
     }
+    if (layout == NQ_LAYOUT_AVAIL) {  // one word per level: the avail field alone
+        if (field != 3) return NQ_EINVAL;
+        *offset_out = nqi::stack_slot_offset((uint32_t)block, (uint32_t)thread, (uint32_t)slot, 4u);
+        return NQ_OK;
+    }
     const bool split = layout == NQ_LAYOUT_WT32 || layout == NQ_LAYOUT_WT32A;
     const uint32_t elem = nqi::stack_elem_bytes(split);
     const uint32_t at = nqi::stack_slot_offset((uint32_t)block, (uint32_t)thread, (uint32_t)slot, elem);

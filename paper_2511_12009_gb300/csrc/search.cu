@@ -360,6 +360,62 @@ __device__ __forceinline__ void step_regm_constr(uint32_t &c, uint32_t &l, uint3
 #undef NQ_PRED_ROWFIELD
 #undef NQ_TAIL
 
+// One step, layout AVAIL (the avail-only stack): one 32-bit word per level,
+// the word of level k of thread t at (k * block + t) * 4 -- every access a
+// word in the lane's own bank. Columns sit at bits 1..N (bit 0 and bits
+// N+1..31 are guard columns, pre-set in cols, so N <= 30). Descending from a
+// level stores that level's candidates with the chosen column still in them
+// (the word's lowest column bit) and, in the word's guard bits, the one bit
+// each diagonal shift drops: bit 0 of rd + p and bit 31 of ld + p. Returning
+// to the level undoes the placement exactly: cols - q, ((ld >> 1) | bit 31) - q,
+// ((rd << 1) | bit 0) - q, and the candidates left are the word's columns
+// minus q. Every level is stored (the undo needs each placement), so a level
+// whose candidates ran out costs a step of its own on the way up (a step with
+// no candidate only pops). The lane's root level lives in registers at top ==
+// base and is never popped: with no candidate left it idles there.
+template <bool DIAG>
+__device__ __forceinline__ void step_avail(uint32_t &c, uint32_t &l, uint32_t &r, uint32_t &av,
+                                           uint32_t &top, const Lane &k, uint32_t &s32,
+                                           uint32_t &n32, const uint32_t m1, const uint32_t m2,
+                                           const uint32_t mneg, const uint32_t mhalf) {
+    const bool pv = av != 0u;
+    const uint32_t p = av & (av * mneg);
+    const uint32_t ar = p * mneg + av;
+    const uint32_t c2 = p * m1 + c;
+    const uint32_t lp = p * m1 + l;
+    const uint32_t rp = p * m1 + r;
+    const uint32_t l2 = lp * m2;
+    const uint32_t r2 = __umulhi(rp, mhalf);
+    const uint32_t a2 = ~(c2 | l2 | r2);
+    const bool lastrow = one_free(c2);          // (never true with p = 0: <= N-2 queens here)
+    const bool live = a2 != 0u;
+    s32 += (lastrow && live) ? 1u : 0u;
+    if (DIAG) n32 += pv ? 1u : 0u;              // a step with a candidate places a queen
+    const bool push = pv && !lastrow && live;
+    const bool pop = !push && ar == 0u && top != k.base;
+    if (push) {
+        if (!DIAG || top < k.limit) {
+            sts1(top, av | (rp & 1u) | (lp & 0x80000000u));
+            top += k.stride;
+            c = c2; l = l2; r = r2; av = a2;
+        } else {
+            record_error(k.status, NQ_ESTACK);
+            av = 0u;
+        }
+    } else if (pop) {
+        top -= k.stride;
+        const uint32_t w = lds1(top);
+        const uint32_t v = w & 0x7FFFFFFEu;           // the level's candidates, q included
+        const uint32_t qn = (v & (v * mneg)) * mneg;  // -q
+        c = c + qn;
+        l = (__umulhi(l, mhalf) | (w & 0x80000000u)) + qn;
+        r = ((r * m2) | (w & 1u)) + qn;
+        av = v + qn;
+    } else {
+        av = ar;
+    }
+}
+
 // One step, layout WT (write-through): the top frame lives in registers AND in
 // its stack slot. The child is computed in place; when it is pushed it is
 // written through to the next slot (after the parent's slot gets its
@@ -549,11 +605,12 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
     constexpr bool kPushLast = LAYOUT == NQ_LAYOUT_REGP || LAYOUT == NQ_LAYOUT_REGPZ;
     constexpr bool kSplit = LAYOUT == NQ_LAYOUT_REGZ || LAYOUT == NQ_LAYOUT_REGPZ;
     constexpr bool kReg = LAYOUT == NQ_LAYOUT_REG || kRegm;
+    constexpr bool kAvail = LAYOUT == NQ_LAYOUT_AVAIL;
     constexpr bool kWt = LAYOUT == NQ_LAYOUT_WT;
     constexpr bool kWt32 = LAYOUT == NQ_LAYOUT_WT32 || LAYOUT == NQ_LAYOUT_WT32A;
     constexpr bool kWtm = LAYOUT == NQ_LAYOUT_WTM;
     constexpr bool kArith = LAYOUT == NQ_LAYOUT_WT32A || kWtm || kRegm;  // alternating sentinel
-    constexpr bool kRegs = kReg || kWt || kWt32 || kWtm;  // top frame held in registers
+    constexpr bool kRegs = kReg || kWt || kWt32 || kWtm || kAvail;  // top frame in registers
     // REGM (production and streamed builds) keeps two sentinel frames, in slots
     // 0 and 1: an idle lane then has 32 sentinel steps before it could pop below
     // its stack, so it runs 31 steps between bookkeeping points instead of 15
@@ -562,8 +619,8 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
     constexpr int kSteps = kTwo ? 31 : kChunk;
     static_assert(kSteps < 32, "two 16-step sentinels hold 32 idle steps (54 constrained)");
     static_assert(kReg || !CONSTR, "constrained mode uses the REG layout");
-    static_assert(!(kPushLast || kSplit) || (!CONSTR && !DONATE),
-                  "REGP / REGZ / REGPZ: plain and streamed search only");
+    static_assert(!(kPushLast || kSplit || kAvail) || (!CONSTR && !DONATE),
+                  "REGP / REGZ / REGPZ / AVAIL: plain and streamed search only");
     constexpr uint32_t kElem = stack_elem_bytes(kWt32);  // bytes of one slot in one array
     const uint32_t sbase = (uint32_t)__cvta_generic_to_shared(nq_smem);
     Lane k;
@@ -575,6 +632,9 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
         }
         k.stride = stack_word_offset(true, kZBlock, 0u, 1u, 0u);
         k.base = sbase + stack_word_offset(true, kZBlock, threadIdx.x, 0u, 0u);
+    } else if (kAvail) {  // one 32-bit word per level
+        k.stride = stack_slot_offset(blockDim.x, 0u, 1u, 4u);
+        k.base = sbase + stack_slot_offset(blockDim.x, threadIdx.x, 0u, 4u);
     } else {
         k.stride = stack_slot_offset(blockDim.x, 0u, 1u, kElem);
         k.base = sbase + stack_slot_offset(blockDim.x, threadIdx.x, 0u, kElem);
@@ -606,10 +666,13 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
         sts1(k.base + k.table, sent_lr);
         sts1(k.base + 2u * k.table, sent_lr);
         sts1(k.base + 3u * k.table, sent_av);
-    } else {
+    } else if (!kAvail) {  // (AVAIL keeps no sentinel: an idle lane has no candidate)
         frame_store<kSplit>(k.base, make_uint4(sent_c, sent_lr, sent_lr, sent_av));
         if (kTwo)
             frame_store<kSplit>(k.base + k.stride, make_uint4(sent_c, sent_lr, sent_lr, sent_av));
+    }
+    if (kAvail) {
+        c = l = r = av = 0u;
     }
     if (!kRegs) top = k.base + k.stride;
     const uint32_t idle_top = kRegs ? k.base : k.base + k.stride;
@@ -671,7 +734,8 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
     for (;;) {
         // (two sentinels: idle on either; the registers and top are reset to the
         // upper one, so a whole round of steps fits in the 32 sentinel steps)
-        const bool idle = kTwo ? top <= k.base + k.stride : top == idle_top;
+        const bool idle = kAvail ? (top == k.base && av == 0u)
+                                 : kTwo ? top <= k.base + k.stride : top == idle_top;
         if (idle) {
             if (idx != kNone) {
                 // nodes: the steps taken, plus the last-row placements Algorithm
@@ -680,7 +744,9 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
                 finish(idx, sol, kPushLast ? nod : nod + sol, wt, pn);
                 idx = kNone;
             }
-            if (kRegs) {
+            if (kAvail) {
+                c = l = r = av = 0u;
+            } else if (kRegs) {
                 c = sent_c;
                 l = r = sent_lr;
                 av = sent_av;
@@ -736,10 +802,12 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
                     const bool ok = n >= 1u && (a.expect_n == 0 || (int)n == a.expect_n) &&
                                     (w == 1u || w == 2u) && d <= n && (P.x & ~last) == 0u &&
                                     (uint32_t)__popc(P.x) == d &&
-                                    (!CONSTR || n <= (uint32_t)kMaxConstrainedN);
+                                    (!CONSTR || n <= (uint32_t)kMaxConstrainedN) &&
+                                    (!kAvail || n <= 30u);  // AVAIL: two guard columns
                     const int need_slots =
-                        kReg ? (int)n - 2 - (int)d + (kPushLast ? 1 : 0) + (kTwo ? 2 : 1)
-                             : (int)n - (int)d;
+                        kAvail ? (int)n - 2 - (int)d  // words of rows d..N-3
+                        : kReg ? (int)n - 2 - (int)d + (kPushLast ? 1 : 0) + (kTwo ? 2 : 1)
+                               : (int)n - (int)d;
                     // (REG: sentinel(s) + ancestors of rows d..N-3, or d..N-2 with the
                     // last row pushed; WT / PAPER: sentinel + frames of rows d..N-2)
                     if (!ok) {
@@ -767,7 +835,13 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
                         } else {
                             idx = pi; wt = w; pn = n; sol = 0; nod = 0;
                             k.thr = (n - 1u) << kRowShift;
-                            if (kReg) {
+                            if (kAvail) {  // columns moved up one bit, guards pre-set
+                                c = (P.x << 1) | ~(last << 1);
+                                l = l0 << 1;
+                                r = r0 << 1;
+                                av = ~(c | l | r);
+                                top = k.base;
+                            } else if (kReg) {
                                 c = c0; l = l0; r = r0; av = a0;
                                 top = k.base + (kTwo ? 2u : 1u) * k.stride;  // above the sentinel(s)
                             } else if (kWt || kWtm) {
@@ -975,7 +1049,9 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
         uint32_t s32 = 0, n32 = 0;
 #pragma unroll
         for (int j = 0; j < kSteps; ++j) {
-            if (kRegm && CONSTR && DIAG)
+            if (kAvail)
+                step_avail<DIAG>(c, l, r, av, top, k, s32, n32, m1, m2, mneg, mhalf);
+            else if (kRegm && CONSTR && DIAG)
                 step_reg<DIAG, true, true>(c, l, r, av, top, k, s32, n32, m1, m2, mneg, mhalf);
             else if (kRegm && CONSTR)
                 step_regm_constr(c, l, r, av, top, k.stride, k.table, k.thr, s32, m1, m2, mneg,
@@ -1320,6 +1396,7 @@ void *pick_kernel(int layout, bool diag, bool constrained, bool donate = false,
         case NQ_LAYOUT_REGP: return plain_ptr<NQ_LAYOUT_REGP>(diag);
         case NQ_LAYOUT_REGZ: return plain_ptr<NQ_LAYOUT_REGZ>(diag);
         case NQ_LAYOUT_REGPZ: return plain_ptr<NQ_LAYOUT_REGPZ>(diag);
+        case NQ_LAYOUT_AVAIL: return plain_ptr<NQ_LAYOUT_AVAIL>(diag);
         default: return plain_ptr<NQ_LAYOUT_REG>(diag);
     }
 }
@@ -1332,6 +1409,7 @@ int slots_needed(int layout, int max_n, int min_d) {
     // rows d..N-2; WT / PAPER: a sentinel + frames of rows d..N-2
     int s = reg ? max_n - 1 - min_d : max_n - min_d;
     if (layout == NQ_LAYOUT_REGP || layout == NQ_LAYOUT_REGPZ) s += 1;
+    if (layout == NQ_LAYOUT_AVAIL) s = max_n - 2 - min_d;  // one word per level d..N-3
     if (layout_regm_family(layout)) s = (s < 1 ? 1 : s) + 1;  // the second sentinel frame
     return s < 1 ? 1 : s;
 }
@@ -1354,8 +1432,9 @@ int make_plan(int max_n, int min_d, bool diag, bool constrained, const nq_config
     if (p.block < 32 || p.block > 1024 || p.block % 32) return NQ_EINVAL;
     // split-word kernels are compiled for one block size
     if (layout_split_words(p.layout) && p.block != (int)kZBlock) return NQ_EINVAL;
+    if (p.layout == NQ_LAYOUT_AVAIL && max_n > 30) return NQ_EINVAL;  // guard columns
     p.slots = slots_needed(p.layout, max_n, min_d);
-    const size_t per_thread = (size_t)p.slots * 16u;
+    const size_t per_thread = (size_t)p.slots * (p.layout == NQ_LAYOUT_AVAIL ? 4u : 16u);
     const size_t extra = constrained ? 32u * 4u : 0u;
     if ((size_t)p.block * per_thread + extra > (size_t)max_smem) {
         int fit = (int)(((size_t)max_smem - extra) / per_thread) / 32 * 32;

@@ -20,9 +20,9 @@ NQ_OK, NQ_EINVAL, NQ_ENOMEM, NQ_ECUDA, NQ_EOVERFLOW, NQ_ETIMEOUT, NQ_ESTACK, NQ_
     0, -1, -2, -3, -4, -5, -6, -7)
 NQ_LAYOUT_DEFAULT, NQ_LAYOUT_PAPER, NQ_LAYOUT_REG, NQ_LAYOUT_WT = 0, 1, 2, 3
 NQ_LAYOUT_WT32, NQ_LAYOUT_WT32A, NQ_LAYOUT_WTM, NQ_LAYOUT_REGM = 4, 5, 6, 7
-NQ_LAYOUT_REGP, NQ_LAYOUT_REGZ, NQ_LAYOUT_REGPZ = 8, 9, 10
+NQ_LAYOUT_REGP, NQ_LAYOUT_REGZ, NQ_LAYOUT_REGPZ, NQ_LAYOUT_AVAIL = 8, 9, 10, 11
 LAYOUTS = {"default": 0, "paper": 1, "reg": 2, "wt": 3, "wt32": 4, "wt32a": 5, "wtm": 6,
-           "regm": 7, "regp": 8, "regz": 9, "regpz": 10}
+           "regm": 7, "regp": 8, "regz": 9, "regpz": 10, "avail": 11}
 NQ_MAX_N = 31
 
 # numpy view of nq_prefix {u32 cols, ld, rd, meta}

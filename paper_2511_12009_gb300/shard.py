@@ -48,14 +48,21 @@ class CheckpointError(RuntimeError):
     pass
 
 
-def gpu_counter(device=None, config: nq.Config | None = None) -> Callable[[np.ndarray], np.ndarray]:
-    """Per-prefix solution counts of host records, on this process's GPU."""
+def gpu_counter(device=None, config: nq.Config | None = None,
+                split: bool = False) -> Callable[[np.ndarray], np.ndarray]:
+    """Per-prefix solution counts of host records, on this process's GPU.
+    split: count through nq_count_split (each record expanded a few rows on the
+    host so that a piece of few heavy subtrees still fills the GPU)."""
     import torch
     dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
 
     def count(records: np.ndarray) -> np.ndarray:
         if len(records) == 0:
             return np.zeros(0, dtype=np.uint64)
+        if split:
+            with torch.cuda.device(dev):
+                return np.asarray(nq.count_split(records, -1, config)["counts"],
+                                  dtype=np.uint64).copy()
         d_pre = nq.to_device(records, dev)
         counts = torch.zeros(len(records), dtype=torch.int64, device=dev)
         meta = records["meta"]
@@ -182,12 +189,26 @@ def read_checkpoint(path: str, header: dict) -> Done:
     return done
 
 
+def records_digest(records: np.ndarray) -> str:
+    """sha256 (first 16 hex digits) of a record array: names a sample in a log."""
+    import hashlib
+    return hashlib.sha256(np.ascontiguousarray(records, dtype=nq.PREFIX_DTYPE).tobytes()
+                          ).hexdigest()[:16]
+
+
 def count_board(n: int, d: int | None = None, *, rank: int = 0, world: int = 1,
                 mode: str = "lease", ratios=None, chunk: int = 1 << 16, store=None,
                 job: str = "nq", counter: Callable | None = None, checkpoint: str | None = None,
-                on_piece: Callable[[int, int], None] | None = None) -> dict:
+                on_piece: Callable[[int, int], None] | None = None,
+                records: np.ndarray | None = None) -> dict:
     """Count the N-Queens solutions of an n x n board with `world` workers, this
     process being worker `rank`.
+
+    records: count these subproblems (records of board n) instead of the
+    board's whole depth-d prefix set -- a sample of a board too large to count
+    whole (the paper's 27-Queens run, Section 4.5); d is then the records'
+    smallest depth, "total" their weighted sum, and the checkpoint header also
+    carries the records' digest, so that a log of another sample is refused.
 
     mode "static": worker `rank` counts its nq_partition slice (ratios as
     there, None = uniform) in pieces of at most `chunk` subproblems. mode
@@ -213,9 +234,17 @@ def count_board(n: int, d: int | None = None, *, rank: int = 0, world: int = 1,
         raise ValueError("leasing across workers needs a shared store")
     if counter is None:
         counter = gpu_counter()
-    records = nq.enumerate_prefixes(n, d)
-    m = len(records)
-    header = {"n": int(n), "d": int(d), "records": int(m)}
+    if records is None:
+        records = nq.enumerate_prefixes(n, d)
+        m = len(records)
+        header = {"n": int(n), "d": int(d), "records": int(m)}
+    else:
+        records = np.ascontiguousarray(records, dtype=nq.PREFIX_DTYPE)
+        m = len(records)
+        if m and int(((records["meta"] >> 2) & 31).max()) != n:
+            raise ValueError("records of another board size")
+        d = int(((records["meta"] >> 7) & 31).min()) if m else 0
+        header = {"n": int(n), "d": int(d), "records": int(m), "sample": records_digest(records)}
 
     done = read_checkpoint(checkpoint, header) if checkpoint is not None else Done()
     group = dist.is_available() and dist.is_initialized() and world > 1

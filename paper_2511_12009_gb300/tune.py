@@ -83,8 +83,9 @@ def _depths(n: int, max_records: int) -> list[int]:
     return out or [d0]
 
 
-def tune(n: int, reps: int = 2, max_records: int = 64_000_000, layouts=("regm", "reg", "wt"),
-         blocks=(128, 256, 512), claims=(1, 2, 4), verbose=False) -> dict:
+def tune(n: int, reps: int = 2, max_records: int = 64_000_000,
+         layouts=("regp", "regm", "reg", "wt"), blocks=(128, 192, 256, 512), claims=(1, 2, 4),
+         verbose=False) -> dict:
     """Tune the launch for board size n; returns the best config (also cached)."""
     key = f"{_device_key()}|N={n}"
     tried = []
@@ -132,35 +133,62 @@ def best_config(n: int) -> nq.Config:
     return nq.make_config(**cfg) if cfg else nq.make_config(d=nq.default_depth(n))
 
 
-def tune_batch(ns, reps: int = 2, blocks=(128, 256), claims=(1, 2), verbose=False) -> dict:
-    """Tune a batched launch over boards ns: per-board depths from each board's
-    own tuning (or the default), then block size / order / chunk of the one
-    launch, timed by graph replays. Returns {"ds": [...], "config": {...}, "ms": ...}."""
+def tune_batch(ns, reps: int = 1, layouts=("regp", "regm", "reg"), blocks=(192, 256),
+               claims=(2, 4), depth_offsets=(-1, 1), verbose=False) -> dict:
+    """Tune a batched launch over boards ns, staged like tune(): the prefix
+    depths (every board's tuned or default depth, shifted together by each of
+    depth_offsets), then the stack layout, then the block size (0 = the one
+    keeping the most threads resident) and claim order, then the claim chunk --
+    each stage keeping the best so far. Every candidate is one captured graph
+    timed by its own replays (best of `reps`) and must give the same totals.
+    Returns {"ds": [...], "config": {...}, "ms": ..., "tried": [...]} (cached)."""
     from .batch import Batch
-    ds = []
+    base_ds = []
     for n in ns:
         c = cached(n)
-        ds.append(c["d"] if c else nq.default_depth(n))
-    best, best_ms, ref = None, None, None
-    for layout in ("regm", "reg"):
-        for block in blocks:
-            for order in (0, 1):
-                for claim in claims:
-                    cfg = {"layout": nq.LAYOUTS[layout], "block": block, "blocks_per_sm": 0,
-                           "order": order, "d": 0, "claim": claim}
-                    with Batch(ns, ds, nq.make_config(**cfg)) as b:
-                        ms = None
-                        for _ in range(reps):
-                            tot, t = b.run()
-                            if ref is not None and tot != ref:
-                                raise RuntimeError(f"batch totals differ for {cfg}")
-                            ref = tot
-                            ms = t if ms is None else min(ms, t)
-                    if verbose:
-                        print(f"  batch {cfg} -> {ms:.3f} ms", flush=True)
-                    if best_ms is None or ms < best_ms:
-                        best, best_ms = cfg, ms
-    rec = {"ds": ds, "config": best, "ms": best_ms, "totals": ref}
+        base_ds.append(c["d"] if c else nq.default_depth(n))
+    tried = []
+    ref = None
+
+    def run(ds, cfg):
+        nonlocal ref
+        with Batch(ns, ds, nq.make_config(**cfg)) as b:
+            ms = None
+            for _ in range(reps):
+                tot, t = b.run()
+                if ref is not None and tot != ref:
+                    raise RuntimeError(f"batch totals differ for {ds} {cfg}")
+                ref = tot
+                ms = t if ms is None else min(ms, t)
+        tried.append({"ds": list(ds), **cfg, "ms": ms})
+        if verbose:
+            print(f"  batch ds={ds} {cfg} -> {ms:.3f} ms", flush=True)
+        return ms
+
+    best_ds = list(base_ds)
+    best = {"layout": 0, "block": 0, "blocks_per_sm": 0, "order": 0, "d": 0, "claim": 0}
+    best_ms = run(best_ds, best)
+    for off in depth_offsets:
+        ds = [min(max(1, d + off), max(1, n - 2)) for d, n in zip(base_ds, ns)]
+        if ds != best_ds:
+            ms = run(ds, best)
+            if ms < best_ms:
+                best_ds, best_ms = ds, ms
+
+    def stage(variants):
+        nonlocal best, best_ms
+        for change in variants:
+            cfg = {**best, **change}
+            if cfg == best:
+                continue
+            ms = run(best_ds, cfg)
+            if ms < best_ms:
+                best, best_ms = cfg, ms
+
+    stage([{"layout": nq.LAYOUTS[lay]} for lay in layouts])
+    stage([{"block": b, "order": o} for b in (0,) + tuple(blocks) for o in (0, 1)])
+    stage([{"claim": c} for c in claims])
+    rec = {"ds": best_ds, "config": best, "ms": best_ms, "totals": ref, "tried": tried}
     _store(f"{_device_key()}|batch={','.join(map(str, ns))}", rec)
     return rec
 

@@ -20,7 +20,8 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 Q = {int(k): v for k, v in json.load(open(os.path.join(GOLDEN, "oeis_a000170.json")))["Q"].items()}
-LAYOUTS = ["paper", "reg", "wt", "wt32", "wt32a", "wtm", "regm", "regp", "regz", "regpz"]
+LAYOUTS = ["paper", "reg", "wt", "wt32", "wt32a", "wtm", "regm", "regp", "regz", "regpz",
+           "avail"]
 SPLIT_WORDS = {"regz", "regpz"}  # compiled for 256-thread blocks
 
 
@@ -424,3 +425,13 @@ def test_streamed_total_new_layouts(layout):
     in every register-top layout."""
     r = nq.total_ex(18, nq.make_config(layout, d=7))
     assert r["total"] == Q[18] and r["layout"] == nq.LAYOUTS[layout]
+
+
+def test_avail_only_stack_limits():
+    """AVAIL keeps two guard columns in its 32-bit masks: N <= 30."""
+    pre = nq.enumerate_prefixes(31, 29)[:4]
+    dp = nq.to_device(pre)
+    cnt = torch.zeros(len(pre), dtype=torch.int64, device="cuda")
+    with pytest.raises(nq.NQError) as e:
+        nq.count_ex(dp, 29, 31, cnt, None, None, nq.make_config("avail"))
+    assert e.value.code == nq.NQ_EINVAL

@@ -93,6 +93,7 @@ ACCESSES = {
     "wt32": [(0, 4), (1, 4), (2, 4), (3, 4)], "wt32a": [(0, 4), (1, 4), (2, 4), (3, 4)],
     "regp": [(0, 16)],
     "regz": [(0, 4), (1, 4), (2, 4), (3, 4)], "regpz": [(0, 4), (1, 4), (2, 4), (3, 4)],
+    "avail": [(3, 4)],
 }
 SPLIT_WORDS = {"regz", "regpz"}  # built for 256-thread blocks only
 KNOWN_4WAY = {("wt", 3), ("wtm", 3)}  # the lone avail-word stores of WT and WTM

@@ -201,3 +201,44 @@ def test_single_worker_splits_agree():
         totals.add(shard.count_board(n, d, mode=mode, chunk=chunk,
                                      counter=OracleCounter(n, d))["total"])
     assert totals == {OEIS[n]}
+
+
+def test_sample_of_records_checkpoint_and_refusal(tmp_path):
+    """count_board over an explicit sample (a board too large to count whole):
+    stopped between pieces, resumed with another chunk size, every record
+    counted once and equal to the oracle; a log written for another sample
+    is refused."""
+    n, d = 11, 4
+    counter = OracleCounter(n, d)
+    recs = nq.enumerate_prefixes(n, d)
+    pick = np.random.default_rng(3).permutation(len(recs))[:200]
+    sample = recs[pick]
+    want = counter(sample)
+    ck = str(tmp_path / "ck")
+
+    class Stop(Exception):
+        pass
+
+    seen = []
+
+    def stop_after_two(lo, hi):
+        seen.append((lo, hi))
+        if len(seen) == 2:
+            raise Stop()
+
+    with pytest.raises(Stop):
+        shard.count_board(n, records=sample, chunk=37, counter=counter, checkpoint=ck,
+                          on_piece=stop_after_two)
+    r = shard.count_board(n, records=sample, chunk=50, counter=counter, checkpoint=ck)
+    assert r["resumed"] == 2 * 37 and r["records"] == 200
+    got = np.zeros(200, dtype=np.uint64)
+    covered = np.zeros(200, dtype=bool)
+    for lo, c in shard.read_checkpoint(ck, {"n": n, "d": d, "records": 200,
+                                            "sample": shard.records_digest(sample)}).items():
+        got[lo:lo + len(c)] = c
+        covered[lo:lo + len(c)] = True
+    assert covered.all() and np.array_equal(got, want)
+    assert r["total"] == int(sum(int(m & 3) * int(c) for m, c in zip(sample["meta"], want)))
+    with pytest.raises(shard.CheckpointError):
+        shard.count_board(n, records=sample[::-1].copy(), chunk=50, counter=counter,
+                          checkpoint=ck)

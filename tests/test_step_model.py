@@ -242,3 +242,74 @@ def test_constrained_sentinel_lasts_a_round():
     for _ in range(31):
         state, top, s = step_constrained(state, stack, top, allowed, 5 << ROW_SHIFT)
         assert s == 0 and 0 <= top <= 1
+
+
+# --- the avail-only stack (layout AVAIL) -----------------------------------------
+
+def search_avail(rec, words):
+    """One subproblem on the avail-only stack, the lane running whole 15-step
+    rounds: columns at bits 1..N with guard columns pre-set, one word per level
+    (the level's candidates with the chosen column in them, and the two bits
+    the diagonal shifts drop), the parent state restored exactly by undoing the
+    placement. Returns (solutions, nodes, deepest)."""
+    n = (int(rec["meta"]) >> 2) & 31
+    d = (int(rec["meta"]) >> 7) & 31
+    last = (1 << n) - 1
+    l0, r0 = int(rec["ld"]), int(rec["rd"]) & last
+    c = ((int(rec["cols"]) << 1) | (~(last << 1) & M)) & M
+    l, r = (l0 << 1) & M, (r0 << 1) & M
+    av = ~(c | l | r) & M
+    if d == n:
+        return 1, 0, 0
+    if d + 1 == n or av == 0:
+        s = popc(av)
+        return s, s, 0
+    stack, top, sol, nodes, deepest = [], 0, 0, 0, 0
+    while True:
+        for _ in range(15):
+            pv = av != 0
+            p = av & ((av * M) & M)
+            ar = (p * M + av) & M
+            c2 = (p + c) & M
+            l2 = (l * 2 + p * 2) & M
+            r2 = ((((p + r) & M) * 0x80000000) >> 32)
+            a2 = ~(c2 | l2 | r2) & M
+            lastrow = popc(c2) == 31
+            sol += 1 if (lastrow and a2) else 0
+            nodes += 1 if pv else 0
+            push = pv and not lastrow and a2 != 0
+            if push:
+                # the word: the candidates (p included) at bits 1..N, and in the
+                # guard bits the one bit each shift drops: bit 0 of rd + p, bit 31
+                # of ld + p
+                lp, rp = (l + p) & M, (p + r) & M
+                stack.append(av | (rp & 1) | (lp & 0x80000000))
+                top += 1
+                assert top <= words, "more words than the stack has"
+                deepest = max(deepest, top)
+                c, l, r, av = c2, l2, r2, a2
+            elif ar == 0 and top > 0:
+                top -= 1
+                w = stack.pop()
+                v = w & 0x7FFFFFFE
+                q = v & ((v * M) & M)
+                c = (c - q) & M
+                l = ((((l * 0x80000000) >> 32) | (w & 0x80000000)) - q) & M
+                r = (((r * 2) & M | (w & 1)) - q) & M
+                av = (v - q) & M
+            else:
+                av = ar
+        if top == 0 and av == 0:
+            return sol, nodes + sol, deepest
+
+
+@pytest.mark.parametrize("n,d", [(6, 2), (8, 3), (9, 4), (10, 3), (10, 6), (11, 5), (7, 7),
+                                 (9, 8), (12, 4), (8, 1), (13, 2)])
+def test_avail_only_model_equals_oracle(orc, n, d):
+    pre = nq.enumerate_prefixes(n, d)
+    cols, _ = orc.prefixes(n, d)
+    want, want_nodes = orc.count_prefixes(n, cols)
+    words = max(n - 2 - d, 1)
+    for i, rec in enumerate(pre):
+        sol, nodes, _ = search_avail(rec, words)
+        assert (sol, nodes) == (int(want[i]), int(want_nodes[i])), (n, d, i)
