@@ -116,6 +116,9 @@ __device__ __forceinline__ unsigned int ldcg4b(const void *p) {
     asm volatile("ld.global.cg.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+__device__ __forceinline__ void stcg8(void *p, unsigned long long v) {
+    asm volatile("st.global.cg.u64 [%0], %1;" : : "l"(p), "l"(v) : "memory");
+}
 __device__ __forceinline__ void stcg4(void *p, uint4 v) {
     asm volatile("st.global.cg.v4.u32 [%0], {%1, %2, %3, %4};"
                  :
@@ -717,7 +720,10 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
                 atomicAdd(reinterpret_cast<unsigned long long *>(&a.nodes[i]),
                           (unsigned long long)nodes_below);
         } else {
-            if (a.counts) a.counts[i] = s;
+            if (a.counts) {
+                if (kSplit) stcg8(&a.counts[i], s);  // (global traffic kept out of L1)
+                else a.counts[i] = s;
+            }
             if (DIAG && a.nodes) a.nodes[i] = nodes_below;
         }
         if (a.totals && s) {
@@ -795,8 +801,11 @@ __device__ __forceinline__ void search_body(const SearchArgs &a) {
                 --rem;
                 {
                     const uint64_t pi = a.order ? a.n - 1 - my : my;
-                    const uint4 P = STREAM ? ldcg4(reinterpret_cast<const uint4 *>(a.pre) + pi)
-                                           : __ldg(reinterpret_cast<const uint4 *>(a.pre) + pi);
+                    // split-word kernels keep their global traffic out of L1, whose
+                    // data banks the shared-memory stack uses
+                    const uint4 P = (STREAM || kSplit)
+                                        ? ldcg4(reinterpret_cast<const uint4 *>(a.pre) + pi)
+                                        : __ldg(reinterpret_cast<const uint4 *>(a.pre) + pi);
                     const uint32_t n = (P.w >> 2) & 31u, d = (P.w >> 7) & 31u, w = P.w & 3u;
                     const uint32_t last = (n >= 1u) ? (0xFFFFFFFFu >> (32u - n)) : 0u;
                     const bool ok = n >= 1u && (a.expect_n == 0 || (int)n == a.expect_n) &&
