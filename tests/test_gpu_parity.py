@@ -429,9 +429,9 @@ def test_streamed_total_new_layouts(layout):
 
 def test_avail_only_stack_limits():
     """AVAIL keeps two guard columns in its 32-bit masks: N <= 30."""
-    pre = nq.enumerate_prefixes(31, 29)[:4]
+    pre = nq.prefixes_at_ranks(31, 2, [0, 1, 2, 3])
     dp = nq.to_device(pre)
     cnt = torch.zeros(len(pre), dtype=torch.int64, device="cuda")
     with pytest.raises(nq.NQError) as e:
-        nq.count_ex(dp, 29, 31, cnt, None, None, nq.make_config("avail"))
+        nq.count_ex(dp, 2, 31, cnt, None, None, nq.make_config("avail"))
     assert e.value.code == nq.NQ_EINVAL
