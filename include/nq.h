@@ -122,10 +122,10 @@ typedef struct nq_queen {
 
 /* Launch configuration. Zero in any field selects the default: for layout,
  * block, claim and d the environment variables NQ_LAYOUT (a layout number or
- * name: paper, reg, wt, wt32, wt32a, wtm, regm, regp, regz, regpz, avail), NQ_BLOCK,
- * NQ_CLAIM and NQ_D
- * when set to a valid value, else the library's own default. (Batches take
- * their configuration as given.) */
+ * name: paper, reg, wt, wt32, wt32a, wtm, regm, regp, regz, regpz, avail),
+ * NQ_BLOCK, NQ_CLAIM and NQ_D when set to a valid value, else the library's own
+ * default (layout REGP; the block size keeping the most threads resident per
+ * SM). (Batches take their configuration as given.) */
 typedef struct nq_config {
     int32_t layout;        /* NQ_LAYOUT_* */
     int32_t block;         /* threads per block, a multiple of 32, <= 1024 */
@@ -446,17 +446,20 @@ int nq_probe_smem(int kind, uint32_t lane_mask, int density, int iters, int slot
 /*
  * Byte offset, within a block's dynamic shared memory, of 32-bit field `field`
  * (0 cols, 1 ld, 2 rd, 3 avail) of stack slot `slot` (slot 0 holds a sentinel
- * frame; REGM's production build keeps a second one in slot 1) of
- * thread `thread`, for a block of `block` threads with `slots` slots per
- * thread, in layout `layout` -- the addresses the search kernel computes (the
- * kernel and this call share one definition). Whole-frame layouts (PAPER, REG,
- * REGM, WT, WTM) put slot k of thread t at (k x block + t) x 16 and move
- * frames as 16-byte accesses; WT and WTM also store the avail word alone
- * (4 bytes). WT32 / WT32A keep four arrays of 32-bit words, word k of thread
- * t at (k x block + t) x 4 in each, and make only 4-byte accesses. A host-side
- * bank simulator built on this call checks which accesses are conflict-free.
- * Errors: NQ_EINVAL for any argument out of range (block a multiple of 32 in
- * 32..1024, slots 1..64).
+ * frame; the production builds of REGM, REGP, REGZ and REGPZ keep a second one
+ * in slot 1) of thread `thread`, for a block of `block` threads with `slots`
+ * slots per thread, in layout `layout` (0: the default) -- the addresses the
+ * search kernel computes (the kernel and this call share one definition).
+ * Whole-frame layouts (PAPER, REG, REGM, REGP, WT, WTM) put slot k of thread t
+ * at (k x block + t) x 16 and move frames as 16-byte accesses; WT and WTM also
+ * store the avail word alone (4 bytes). WT32 / WT32A keep four arrays of
+ * 32-bit words, word k of thread t at (k x block + t) x 4 in each. REGZ and
+ * REGPZ (block 256 only) put word j of slot k of thread t at
+ * ((4k + j) x 256 + t) x 4. AVAIL keeps only the avail word of each level,
+ * at (k x block + t) x 4 (field 3; other fields are NQ_EINVAL). The split and
+ * word layouts make only 4-byte accesses. A host-side bank simulator built on
+ * this call checks which accesses are conflict-free. Errors: NQ_EINVAL for any
+ * argument out of range (block a multiple of 32 in 32..1024, slots 1..64).
  */
 int nq_stack_offset(int layout, int block, int slots, int thread, int slot, int field,
                     uint32_t *offset_out);
