@@ -88,6 +88,8 @@ def parse():
                          "launch vs one launch each; served: Poisson request stream; "
                          "probe27: 4096 seeded N=27 subtrees")
     ap.add_argument("--no-n22", action="store_true", help="skip the N=22 solve")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the short batched and served measurements of the default line")
     ap.add_argument("--n22-nodes", action="store_true",
                     help="count the N=22 nodes with the diagnostic build (about 2.5 min)")
     ap.add_argument("--requests", type=int, default=10000, help="served: requests per run")
@@ -535,6 +537,46 @@ def solve_n22(args, sms: int, sm_max: float, local: int) -> dict:
             "paper_ms": 216740, "paper_hw": "1x RTX 4090 (Table 6, best configuration)"}
 
 
+def quick_batched() -> dict:
+    """The batched form beside the plain one, short: one graph replay over the
+    union of N=16..21 (library depths and launch defaults) and the same work as
+    six plain launches, each timed by CUDA events; totals against OEIS."""
+    from paper_2511_12009_gb300.batch import Batch
+    q = json.load(open(os.path.join(ROOT, "tests", "golden", "oeis_a000170.json")))["Q"]
+    ns = [16, 17, 18, 19, 20, 21]
+    with Batch(ns, None, None) as b:
+        info = b.info()
+        totals, graph_ms = b.run()
+        t2, sep_ms = b.run_separate()
+    return {"workload": "union of N=16..21 prefix sets, one persistent launch from a CUDA graph",
+            "records": info["records"], "graph_ms": graph_ms, "separate_launches_ms": sep_ms,
+            "graph_vs_separate": sep_ms / graph_ms,
+            "totals_exact": totals == t2 == [q[str(n)] for n in ns]}
+
+
+def quick_served(requests: int = 300) -> dict:
+    """The served form, short: a seeded stream of `requests` (N uniform in
+    [10, 20], 0-4 queens) all due at once; requests/s and latency; answers
+    without queens against OEIS and the row-sum identity at N = 17, 18."""
+    import synth_inputs
+    from paper_2511_12009_gb300.serve import Server, run_stream
+    q = json.load(open(os.path.join(ROOT, "tests", "golden", "oeis_a000170.json")))["Q"]
+    reqs = [dict(r, t=0.0) for r in synth_inputs.request_stream(2024, requests, 10, 20, 0, 4, 1.0)]
+    with Server(max_n=20, request_slots=64, idle_ms=200) as srv:
+        res = run_stream(srv, reqs, timeout_s=900)
+        srv.poll()
+    lat = list(res["latency_s"].values())
+    bad = [i for i, r in enumerate(reqs)
+           if not r["queens"] and res["answers"][i] != q[str(r["n"])]]
+    sums = served_row_sums(ns=(17, 18))
+    return {"workload": f"{requests} seeded requests, N uniform in [10, 20], 0-4 queens, "
+                        "all due at once", "requests_per_s": requests / res["wall_s"],
+            "wall_s": res["wall_s"], "p50_ms": 1e3 * float(np.percentile(lat, 50)),
+            "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+            "unconstrained_vs_oeis": sum(1 for r in reqs if not r["queens"]),
+            "row_sums": sums, "exact": not bad and all(x["exact"] for x in sums)}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -656,6 +698,15 @@ def main():
     n22 = None
     if rank == 0 and not args.no_n22 and args.n == 18:
         n22 = solve_n22(args, sms, sm_max, local)
+    # short batched and served measurements (a failure is recorded, not fatal:
+    # the line above is the benchmark)
+    extras = {}
+    if rank == 0 and not args.no_extras and args.n == 18:
+        for name, fn in (("batched", quick_batched), ("served", quick_served)):
+            try:
+                extras[name] = fn()
+            except Exception as e:  # noqa: BLE001
+                extras[name] = {"error": f"{type(e).__name__}: {e}"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -674,7 +725,7 @@ def main():
                            "parallelism": f"replicas x{world}"},
                 "solve_ms": ms_per_step, "total": total_q, "wall_s": t_wall,
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk,
-                "n22": n22, "gpu_launches": args.steps}
+                "n22": n22, **extras, "gpu_launches": args.steps}
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
