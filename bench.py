@@ -434,7 +434,7 @@ def run_served(args, device, local):
             "data": "synthetic",
             "config": {"workload": f"served: {len(reqs)} seeded requests, N uniform in [10, 20], "
                                    "0-4 non-attacking queens, Poisson arrivals",
-                       "request_slots": 64, "stack_slots": 12},
+                       "request_slots": 64, "stack_slots": 13},
             "runs": runs, "answers": check, "answers_exact": check["exact"], "clocks": clk}
     print(json.dumps(line), flush=True)
 

@@ -333,7 +333,7 @@ typedef struct nq_server nq_server;
 typedef struct nq_server_config {
     int32_t max_n;          /* largest board accepted (<= 26; 0: 20) */
     int32_t request_slots;  /* requests in flight at once (<= 256; 0: 64) */
-    int32_t stack_slots;    /* stack frames per lane (0: 12). Admission by footprint: a
+    int32_t stack_slots;    /* stack frames per lane (0: 13). Admission by footprint: a
                                request's prefix depth d is raised until N-1-d frames fit */
     int32_t block;          /* threads per block (0: 256) */
     uint64_t ring_records;  /* subproblem ring capacity, a power of two >= 1024 (0: 2^25) */

@@ -164,7 +164,10 @@ extern "C" int nq_server_create(const nq_server_config *cfg, nq_server **out) {
     nq_server_config c = *cfg;
     if (c.max_n == 0) c.max_n = 20;
     if (c.request_slots == 0) c.request_slots = 64;
-    if (c.stack_slots == 0) c.stack_slots = 12;
+    // 13 frames: an unconstrained N = 20 request then needs depth 6 (3.0 M records,
+    // 9 % of the default ring) instead of 7 (22.8 M, 68 %: one such request at a
+    // time), at the same 3 resident blocks of 256 per SM
+    if (c.stack_slots == 0) c.stack_slots = 13;
     if (c.block == 0) c.block = 256;
     if (c.ring_records == 0) c.ring_records = 1ull << 25;
     if (c.idle_ms == 0) c.idle_ms = 200;

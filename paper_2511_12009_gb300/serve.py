@@ -44,7 +44,7 @@ def _declare():
 
 
 class Server:
-    def __init__(self, max_n=20, request_slots=64, stack_slots=12, block=256,
+    def __init__(self, max_n=20, request_slots=64, stack_slots=0, block=256,
                  ring_records=1 << 25, idle_ms=200):
         lib = _declare()
         cfg = ServerConfig(int(max_n), int(request_slots), int(stack_slots), int(block),
