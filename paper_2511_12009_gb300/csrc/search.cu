@@ -1477,8 +1477,14 @@ int make_plan(int max_n, int min_d, bool diag, bool constrained, const nq_config
         if (best) p.block = best;
     }
     p.smem = (size_t)p.block * per_thread + extra;
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem) !=
-        cudaSuccess)
+    // The kernel's dynamic shared-memory limit is one attribute per kernel, and
+    // plans made earlier (a batch's per-board plans, other callers) may still
+    // be launched: raise it when this plan needs more, never lower it.
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, k) != cudaSuccess) return NQ_ECUDA;
+    if (fa.maxDynamicSharedSizeBytes < (int)p.smem &&
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.smem) !=
+            cudaSuccess)
         return NQ_ECUDA;
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, p.block, p.smem) != cudaSuccess)
@@ -1517,8 +1523,11 @@ int serve_plan(int max_n, int min_d, int nslots, int block, int *grid, size_t *s
     const size_t bytes = (size_t)sl * 16u * block + (size_t)nslots * 132u;
     if (bytes > (size_t)max_smem) return NQ_ESTACK;
     void *k = reinterpret_cast<void *>(&serve_kernel);
-    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
-        cudaSuccess)
+    cudaFuncAttributes fa{};  // (raise only: another server may still relaunch with its size)
+    if (cudaFuncGetAttributes(&fa, k) != cudaSuccess) return NQ_ECUDA;
+    if (fa.maxDynamicSharedSizeBytes < (int)bytes &&
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+            cudaSuccess)
         return NQ_ECUDA;
     int nb = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k, block, bytes) != cudaSuccess)

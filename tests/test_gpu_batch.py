@@ -87,3 +87,15 @@ def test_tuner_finds_a_correct_config(tmp_path, monkeypatch):
     assert r["total"] == Q[13]
     rec = tune.tune_batch([10, 11, 12], reps=1, blocks=(128,), claims=(1,))
     assert rec["totals"] == [Q[10], Q[11], Q[12]]
+
+
+def test_separate_launches_after_planning_every_board():
+    """Planning several boards, then launching them: the board planned last
+    (N=15 at depth 1: 15 frames, the planner picks 224-thread blocks) needs less
+    shared memory per block than one planned before it (N=14 at depth 1: 14
+    frames, 256-thread blocks). Every launch must still be valid."""
+    from paper_2511_12009_gb300.batch import Batch
+    with Batch([14, 15], [1, 1], None) as b:
+        totals, _ = b.run()
+        sep, _ = b.run_separate()
+    assert totals == sep == [Q[14], Q[15]]
