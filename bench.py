@@ -89,7 +89,7 @@ def parse():
                          "probe27: 4096 seeded N=27 subtrees")
     ap.add_argument("--no-n22", action="store_true", help="skip the N=22 solve")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the short batched and served measurements of the default line")
+                    help="skip the short N=14, batched and served measurements of the default line")
     ap.add_argument("--n22-nodes", action="store_true",
                     help="count the N=22 nodes with the diagnostic build (about 2.5 min)")
     ap.add_argument("--requests", type=int, default=10000, help="served: requests per run")
@@ -537,6 +537,24 @@ def solve_n22(args, sms: int, sm_max: float, local: int) -> dict:
             "paper_ms": 216740, "paper_hw": "1x RTX 4090 (Table 6, best configuration)"}
 
 
+def solve_n14(reps: int = 50) -> dict:
+    """The smallest configured workload, N = 14 at the library's depth: a
+    latency probe. `reps` exact solves through nq_total_ex (enumerate, upload,
+    search, total back), median wall and kernel times."""
+    from paper_2511_12009_gb300 import nq
+    nq.total_ex(14)  # warm
+    walls, kerns, exact = [], [], True
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        r = nq.total_ex(14)
+        walls.append(1e3 * (time.perf_counter() - t0))
+        kerns.append(r["kernel_ms"])
+        exact = exact and r["total"] == 365596
+    return {"workload": f"N=14 full count, d={r['d']} ({r['prefixes']} subproblems)",
+            "reps": reps, "solve_ms_median": float(np.median(walls)),
+            "kernel_ms_median": float(np.median(kerns)), "exact": exact}
+
+
 def quick_batched() -> dict:
     """The batched form beside the plain one, short: one graph replay over the
     union of N=16..21 (library depths and launch defaults) and the same work as
@@ -702,7 +720,8 @@ def main():
     # the line above is the benchmark)
     extras = {}
     if rank == 0 and not args.no_extras and args.n == 18:
-        for name, fn in (("batched", quick_batched), ("served", quick_served)):
+        for name, fn in (("n14", solve_n14), ("batched", quick_batched),
+                         ("served", quick_served)):
             try:
                 extras[name] = fn()
             except Exception as e:  # noqa: BLE001
