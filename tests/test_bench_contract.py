@@ -56,3 +56,27 @@ def test_reference_arm_does_not_load_the_library():
                        timeout=300)
     assert r.returncode == 0, r.stderr[-2000:]
     assert r.stdout.strip().splitlines()[-1] == "CLEAN"
+
+
+def test_served_answer_check_catches_a_wrong_answer():
+    """The served bench's exactness check: answers equal to OEIS for boards
+    without queens and to the oracle for a seeded sample pass; one wrong
+    answer in either group fails it. (Small stream, boards N <= 12.)"""
+    sys.path.insert(0, ROOT)
+    import bench
+    import oracle
+    import synth_inputs
+    oracle.build()
+    reqs = synth_inputs.request_stream(7, 60, 6, 12, 0, 3, rate_per_s=1.0)
+    q = json.load(open(os.path.join(ROOT, "tests", "golden", "oeis_a000170.json")))["Q"]
+    right = {i: (q[str(r["n"])] if not r["queens"] else oracle.count_constrained(r["n"], r["queens"])[0])
+             for i, r in enumerate(reqs)}
+    chk = bench.check_served_answers(reqs, right, sample=1000, n16=0)
+    assert chk["exact"] and chk["mismatches"] == 0
+    assert chk["constrained_vs_oracle"] == sum(1 for r in reqs if r["queens"])
+    k0 = next(i for i, r in enumerate(reqs) if not r["queens"])
+    k1 = next(i for i, r in enumerate(reqs) if r["queens"])
+    for i in (k0, k1):
+        wrong = dict(right)
+        wrong[i] += 1
+        assert not bench.check_served_answers(reqs, wrong, sample=1000, n16=0)["exact"]
