@@ -475,6 +475,18 @@ def run_probe27(args, device, local):
     e1.record(stream)
     nq.sync(stream)
     direct_ms = e0.elapsed_time(e1) / args.steps
+    # the same launch with subtree donation (idle lanes take shallow frames of busy ones)
+    don_cfg = nq.make_config(donate=2)
+    cnt_d = torch.zeros(k, dtype=torch.int64, device=device)
+    nq.count_ex(pre, d0 + extra, n, cnt_d, None, None, don_cfg, stream)
+    nq.sync(stream)
+    donate_exact = np.array_equal(cnt_d.cpu().numpy().view(np.uint64), want)
+    e0.record(stream)
+    for _ in range(args.steps):
+        nq.count_ex(pre, d0 + extra, n, cnt_d, None, None, don_cfg, stream)
+    e1.record(stream)
+    nq.sync(stream)
+    donate_ms = e0.elapsed_time(e1) / args.steps
     # host split: each subtree expanded on the host until every lane has work
     split = nq.count_split(host_pre, -1)
     clocks.start()
@@ -490,7 +502,8 @@ def run_probe27(args, device, local):
                        "split_rows": split["rows"], "split_children": split["children"],
                        "split_host_ms": min(r["split_ms"] for r in runs),
                        "split_call_ms": min(r["total_ms"] for r in runs),
-                       "unsplit_kernel_ms": direct_ms, "counts_equal_unsplit": exact},
+                       "unsplit_kernel_ms": direct_ms, "counts_equal_unsplit": exact,
+                       "donation_kernel_ms": donate_ms, "donation_counts_exact": donate_exact},
             "clocks": clk, "gpu_launches": args.steps}
     print(json.dumps(line), flush=True)
 
