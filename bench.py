@@ -475,8 +475,9 @@ def run_probe27(args, device, local):
     e1.record(stream)
     nq.sync(stream)
     direct_ms = e0.elapsed_time(e1) / args.steps
-    # the same launch with subtree donation (idle lanes take shallow frames of busy ones)
-    don_cfg = nq.make_config(donate=2)
+    # the same launch with subtree donation (idle lanes take shallow frames of busy ones;
+    # donation is built for the REG and REGM forms, so REGM here)
+    don_cfg = nq.make_config("regm", donate=2)
     cnt_d = torch.zeros(k, dtype=torch.int64, device=device)
     nq.count_ex(pre, d0 + extra, n, cnt_d, None, None, don_cfg, stream)
     nq.sync(stream)
